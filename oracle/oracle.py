@@ -1,0 +1,177 @@
+"""ctypes front end of the plain C oracle (test infrastructure only).
+
+The C sources beside this file implement the paper's Algorithms 1-3 literally (``route_a.c``) and an
+independently derived reduced form of the same iteration (``route_r.c``).  ``build()`` compiles them with
+gcc into ``oracle/_build/liboracle.so``; nothing here touches a GPU.
+
+Array conventions: every polynomial array is a coefficient list in descending lexicographic order of the
+exponent tuple (x1 exponent descending, then x2, then x3), the order in which the paper prints quartics.
+"""
+import ctypes
+import os
+import subprocess
+from math import comb
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
+_lib = None
+
+__all__ = ["build", "lib", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
+           "stage_arrays_a", "stage_arrays_r", "ROUTE_A", "ROUTE_R"]
+
+ROUTE_A = 0
+ROUTE_R = 1
+
+
+def build(force=False):
+    """Compile the oracle with gcc (portable C11, no architecture flags) and return the library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "hpoly.h")])
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        L.qfs_oracle_height_a.argtypes = [ctypes.c_int, u8p, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p]
+        L.qfs_oracle_height_a.restype = ctypes.c_int
+        L.qfs_oracle_height_r.argtypes = [ctypes.c_int, u8p, ctypes.c_int, i32p, i32p]
+        L.qfs_oracle_height_r.restype = ctypes.c_int
+        L.qfs_oracle_heights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, u8p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.qfs_oracle_heights.restype = ctypes.c_int
+        L.qfs_oracle_delta1.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, i32p, i32p]
+        L.qfs_oracle_delta1.restype = ctypes.c_int
+        L.qfs_oracle_split_u.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p]
+        L.qfs_oracle_split_u.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def monomial_count(d):
+    """Number of degree-d monomials in four variables, C(d+3, 3)."""
+    return comb(d + 3, 3) if d >= 0 else 0
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+def _quartic(f):
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.uint8).reshape(35))
+    return f
+
+
+def height_a(p, f, max_h=10, lift_signed=False):
+    """Route A (literal Algorithms 1-3) height of one quartic given as 35 coefficients."""
+    f = _quartic(f)
+    return lib().qfs_oracle_height_a(p, _ptr(f, ctypes.c_uint8), max_h, int(lift_signed), None, None, None, None)
+
+
+def height_r(p, f, max_h=10):
+    """Route R (reduced derivation) height of one quartic."""
+    f = _quartic(f)
+    return lib().qfs_oracle_height_r(p, _ptr(f, ctypes.c_uint8), max_h, None, None)
+
+
+def stage_arrays_a(p, f, max_h=10, lift_signed=False):
+    """Route A with every intermediate array: returns dict(h, g, D, delta, iters).
+
+    g = f^(p-1) mod p; D = lift(g)^p mod p^2; delta = Delta_1(g) mod p; iters[h-2] = g_h.
+    D and delta are None when the height-1 test succeeds; iters holds the rows that were computed.
+    """
+    f = _quartic(f)
+    ld = monomial_count(4 * (p - 1))
+    lD = monomial_count(4 * p * (p - 1))
+    g = np.zeros(ld, np.int32)
+    D = np.zeros(lD, np.int32)
+    delta = np.zeros(lD, np.int32)
+    iters = np.zeros((max(max_h - 1, 1), ld), np.int32)
+    h = lib().qfs_oracle_height_a(p, _ptr(f, ctypes.c_uint8), max_h, int(lift_signed), _ptr(g, ctypes.c_int32),
+                                  _ptr(D, ctypes.c_int32), _ptr(delta, ctypes.c_int32), _ptr(iters, ctypes.c_int32))
+    out = dict(h=h, g=g, D=None, delta=None, iters=iters[:0])
+    if h != 1 and h >= 0:
+        out["D"], out["delta"] = D, delta
+        n_rows = (h - 1) if h >= 2 else _rows_until_zero_or_end(iters, p, max_h)
+        out["iters"] = iters[:n_rows]
+    return out
+
+
+def stage_arrays_r(p, f, max_h=10):
+    """Route R with Delta_1(f) and the iterates: returns dict(h, d1f, iters)."""
+    f = _quartic(f)
+    ld = monomial_count(4 * (p - 1))
+    l4p = monomial_count(4 * p)
+    d1f = np.zeros(l4p, np.int32)
+    iters = np.zeros((max(max_h - 1, 1), ld), np.int32)
+    h = lib().qfs_oracle_height_r(p, _ptr(f, ctypes.c_uint8), max_h, _ptr(d1f, ctypes.c_int32),
+                                  _ptr(iters, ctypes.c_int32))
+    out = dict(h=h, d1f=None, iters=iters[:0])
+    if h != 1 and h >= 0:
+        out["d1f"] = d1f
+        n_rows = (h - 1) if h >= 2 else _rows_until_zero_or_end(iters, p, max_h)
+        out["iters"] = iters[:n_rows]
+    return out
+
+
+def _rows_until_zero_or_end(iters, p, max_h):
+    # height 0: the loop ran until an iterate vanished or until max_h
+    for r in range(max_h - 1):
+        if not iters[r].any():
+            return r + 1
+    return max_h - 1
+
+
+def heights(p, coeffs, max_h=10, route=ROUTE_R, threads=None):
+    """Heights of n quartics (uint8 array n x 35) on a pthread pool; returns int8 array of codes."""
+    coeffs = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint8).reshape(-1, 35))
+    n = coeffs.shape[0]
+    out = np.zeros(n, np.int8)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    lib().qfs_oracle_heights(route, p, n, _ptr(coeffs, ctypes.c_uint8), max_h, _ptr(out, ctypes.c_int8), threads)
+    return out
+
+
+def delta1(p, g, deg, lift_signed=False):
+    """Algorithm 1 on an arbitrary form g of degree deg (coefficients mod p, descending lex).
+
+    Returns (D, delta): D = lift(g)^p mod p^2 and Delta_1(g) mod p, both of degree p*deg.
+    Raises ArithmeticError if the division by p is not exact.
+    """
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.int32).reshape(monomial_count(deg)))
+    n = monomial_count(p * deg)
+    D = np.zeros(n, np.int32)
+    delta = np.zeros(n, np.int32)
+    rc = lib().qfs_oracle_delta1(p, deg, _ptr(g, ctypes.c_int32), int(lift_signed), _ptr(D, ctypes.c_int32),
+                                 _ptr(delta, ctypes.c_int32))
+    if rc == -2:
+        raise ArithmeticError("division by p in Algorithm 1 is not exact")
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return D, delta
+
+
+def split_u(p, P, deg):
+    """Algorithm 2 on a form P of degree deg.  Returns (out_degree, coefficients) or (None, None)."""
+    rem = deg - 4 * (p - 1)
+    if rem < 0 or rem % p:
+        return None, None
+    P = np.ascontiguousarray(np.asarray(P, dtype=np.int32).reshape(monomial_count(deg)))
+    out = np.zeros(monomial_count(rem // p), np.int32)
+    d = lib().qfs_oracle_split_u(p, deg, _ptr(P, ctypes.c_int32), _ptr(out, ctypes.c_int32))
+    return d, out
