@@ -1,0 +1,135 @@
+/*
+ * libqfs -- quasi-F-split (Artin-Mazur) heights of quartic K3 surfaces over F_p on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (paper: "K3 surfaces of any Artin-Mazur height over F5 and F7 via quasi-F-split singularities
+ * and GPU acceleration", arXiv 2502.12428):
+ *   for each quartic f in F_p[x1,x2,x3,x4]
+ *     g <- f^(p-1);  if the coefficient of (x1 x2 x3 x4)^(p-1) in g is nonzero, the height is 1
+ *                                                   (Fedder's criterion, Sec. 2.2; matrix-based algorithm, Sec. 3.4)
+ *     Delta <- Delta_1(f^(p-1)) = (lift(g)^p - sum over terms t of lift(g) of t^p) / p  mod p
+ *                                                   (Proposition and Algorithm 1 of Sec. 3.1)
+ *     for h = 2 .. max_h:  g <- u(Delta * g)  (Algorithm 2, the splitting u, Sec. 3.2);  test as above
+ *                                                   (Algorithm 3 / matrix-based algorithm of Sec. 3.3-3.4)
+ *   K3 heights are at most 10 or infinite (Sec. 3.3), so max_h = 10 decides every nonsingular quartic.
+ *
+ * Conventions shared by every entry point:
+ *   - A quartic is 35 uint8 coefficients in descending lexicographic order of (e1, e2, e3, e4):
+ *     x1^4, x1^3 x2, x1^3 x3, x1^3 x4, x1^2 x2^2, ..., x4^4 (the order the paper prints, Figures 4-7).
+ *     `coeffs` is row-major n x 35.  Values must lie in [0, p).
+ *   - Output codes (int8, one per quartic): 1..max_h = the height; 0 = infinity / no witness up to max_h;
+ *     -1 = the row has a coefficient >= p (nothing else is computed for it).
+ *   - Pointers named "device" are CUDA device memory owned by the caller; the library never frees them.
+ *   - Work is stream-ordered on `stream` (a cudaStream_t; NULL = the legacy default stream).  Calls return after
+ *     enqueue; results are valid once the stream reaches that point.  No call synchronises the host unless stated.
+ *   - Errors that can be seen on the host are returned synchronously and nothing is enqueued.  n = 0 is a no-op.
+ *   - The library owns its workspaces (one set per device, grown on demand, freed by qfs_shutdown).  Growing a
+ *     workspace calls cudaMalloc; call qfs_plan_prepare for the largest p and batch first when capturing the
+ *     calls into a CUDA graph.
+ *   - Calls are not thread-safe with respect to each other on the same device.
+ */
+#ifndef QFS_H
+#define QFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every entry point. */
+enum {
+  QFS_OK = 0,
+  QFS_ERR_INVALID_P = 1,      /* p is not one of 3, 5, 7, 11, 13 */
+  QFS_ERR_INVALID_MAX_H = 2,  /* max_h outside [1, 10] */
+  QFS_ERR_INVALID_N = 3,      /* n < 0, or a group count outside [1, QFS_MAX_GROUPS] */
+  QFS_ERR_NULL = 4,           /* a required pointer is NULL */
+  QFS_ERR_NO_MEMORY = 5,      /* the workspace for even one quartic in flight does not fit */
+  QFS_ERR_CUDA = 6,           /* a CUDA runtime call failed; qfs_last_cuda_error() has the code */
+  QFS_ERR_FORM = 7,           /* unknown arithmetic form or engine */
+  QFS_ERR_DEVICE = 8,         /* the current device is not sm_103 */
+  QFS_ERR_CHECK = 9           /* a device-side consistency check failed (see qfs_read_status) */
+};
+
+/* Arithmetic forms of the contractions (all exact; they produce identical results). */
+enum {
+  QFS_FORM_INT32 = 0,   /* int32 multiply-add on CUDA cores (IMAD) */
+  QFS_FORM_DP4A = 1,    /* 4-way int8 dot products with int32 accumulation on CUDA cores (IDP4A) */
+  QFS_FORM_INT8TC = 2   /* int8 tensor cores (mma.sync m16n8k32 s8 -> s32), int32 accumulation */
+};
+
+/* Engines: how the per-quartic stages are scheduled. */
+enum {
+  QFS_ENGINE_FUSED = 0,   /* one persistent launch, work stealing over quartics, every stage fused per quartic */
+  QFS_ENGINE_STAGED = 1   /* one kernel per stage (power, Delta_1, theta, test) over batches of survivors */
+};
+
+#define QFS_MAX_GROUPS 8
+
+/* One batch of quartics over one prime (all pointers device memory owned by the caller). */
+typedef struct {
+  int p;                   /* 3, 5, 7, 11 or 13 */
+  int64_t n;               /* number of quartics, >= 0 */
+  const uint8_t *coeffs;   /* device, n x 35 uint8, row-major, descending lex, values in [0, p) */
+  int8_t *heights_out;     /* device, n int8 */
+} qfs_group_t;
+
+/* Per-call options.  Zero-initialised fields mean "library default". */
+typedef struct {
+  int form;                  /* QFS_FORM_*; -1 = process default (qfs_set_default_form) */
+  int engine;                /* QFS_ENGINE_*; -1 = QFS_ENGINE_FUSED */
+  int ctas_per_sm;           /* fused engine: resident CTAs per SM, 0 = auto */
+  int max_ctas;              /* cap on persistent CTAs (admission), 0 = no cap beyond memory */
+  size_t workspace_budget;   /* bytes of device workspace the call may use, 0 = library default */
+} qfs_options_t;
+
+/* Heights of n quartics over F_p.  coeffs: device, n x 35 uint8.  heights_out: device, n int8.
+   Returns QFS_OK or an error status (nothing enqueued on error). */
+int qfs_heights(int p, int64_t n, const uint8_t *coeffs, int max_h, int8_t *heights_out, cudaStream_t stream);
+
+/* Several batches, possibly over different primes, in one persistent launch (groups is a host array of
+   n_groups <= QFS_MAX_GROUPS descriptors).  Work is ordered largest p first so the heaviest quartics start
+   early.  Same return convention as qfs_heights. */
+int qfs_heights_multi(int n_groups, const qfs_group_t *groups, int max_h, cudaStream_t stream);
+
+/* qfs_heights_multi with explicit options (opts may be NULL). */
+int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, const qfs_options_t *opts,
+                         cudaStream_t stream);
+
+/* Sets the process-wide default form used when opts->form is -1 (initially QFS_FORM_DP4A). */
+int qfs_set_default_form(int form);
+
+/* Prepares the current device for prime p: checks the device, tunes launch shapes and allocates the workspace
+   a fused launch over up to n_hint quartics needs (n_hint <= 0: a full-device launch).  Synchronous; it may call
+   cudaMalloc.  Optional: the first qfs_heights call does the same lazily. */
+int qfs_plan_prepare(int p, int64_t n_hint);
+
+/* Frees every workspace of every device this process used.  Synchronous. */
+int qfs_shutdown(void);
+
+/* Copies the device status word of the current device's last launches into *status_out (0 = no check failed;
+   bit 0 = an exact division by p in Delta_1 found a remainder; bit 1 = the theta test saw an out-of-range value),
+   then clears it.  Synchronises the current device. */
+int qfs_read_status(uint32_t *status_out);
+
+/* Human-readable text for a status code (static storage). */
+const char *qfs_strerror(int status);
+
+/* The cudaError_t of the last failed CUDA call inside the library (0 if none). */
+int qfs_last_cuda_error(void);
+
+/* Kernel-level parity hook (tests only need it; it runs the same device code as qfs_heights on ONE quartic).
+   coeffs: device, 35 uint8.  All outputs are device int32 arrays in descending-lex order; any may be NULL.
+     g_out     C(4p-1,3) values: f^(p-1) mod p
+     G_out     C(4p(p-1)+3,3) values: f~^(p(p-1)) mod p^2 (equal to lift(g)^p mod p^2), only if height != 1
+     delta_out C(4p(p-1)+3,3) values: Delta_1(f^(p-1)) mod p, only if height != 1
+     iters_out (max_h-1) x C(4p-1,3): row h-2 = the iterate g_h, for the rows computed
+   height_out: device, 1 int8 (the same code qfs_heights writes).  Synchronous. */
+int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
+                     int32_t *delta_out, int32_t *iters_out, int8_t *height_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QFS_H */

@@ -1,0 +1,360 @@
+// libqfs host runtime: argument checks, per-device workspaces, admission by device memory, launches.
+// The C ABI is declared (and documented) in include/qfs.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/qfs.h"
+#include "qfs_kernels.cuh"
+
+namespace qfs {
+
+namespace {
+
+struct DeviceState {
+  bool init = false;
+  bool supported = false;
+  int sms = 0;
+  size_t total_mem = 0;
+  void *ws = nullptr;          // persistent-CTA workspaces
+  size_t ws_bytes = 0;
+  void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32)
+};
+
+constexpr int kMaxDevices = 64;
+DeviceState g_dev[kMaxDevices];
+std::mutex g_mu;
+int g_default_form = QFS_FORM_DP4A;
+int g_last_cuda = 0;
+
+bool valid_p(int p) { return p == 3 || p == 5 || p == 7 || p == 11 || p == 13; }
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return QFS_ERR_CUDA;
+}
+
+int device_state(DeviceState **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxDevices) return QFS_ERR_DEVICE;
+  DeviceState &S = g_dev[dev];
+  if (!S.init) {
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    S.sms = prop.multiProcessorCount;
+    S.total_mem = prop.totalGlobalMem;
+    S.supported = (prop.major == 10 && prop.minor == 3);
+    e = cudaMalloc(&S.ctrl, 64);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemset(S.ctrl, 0, 64);
+    if (e != cudaSuccess) return cuda_fail(e);
+    S.init = true;
+  }
+  if (!S.supported) return QFS_ERR_DEVICE;
+  *out = &S;
+  return QFS_OK;
+}
+
+int ensure_workspace(DeviceState &S, size_t bytes) {
+  if (S.ws_bytes >= bytes) return QFS_OK;
+  if (S.ws) {
+    cudaError_t e = cudaFree(S.ws);
+    S.ws = nullptr;
+    S.ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  cudaError_t e = cudaMalloc(&S.ws, bytes);
+  if (e != cudaSuccess) {
+    S.ws = nullptr;
+    (void)cudaGetLastError();
+    return QFS_ERR_NO_MEMORY;
+  }
+  S.ws_bytes = bytes;
+  return QFS_OK;
+}
+
+cudaError_t form_occupancy(int form, int *blocks, size_t smem) {
+  switch (form) {
+    case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem);
+    default: return FormLauncher<1>::occupancy(blocks, smem);
+  }
+}
+
+cudaError_t form_fused(int form, const FusedParams &prm, int grid, size_t smem, cudaStream_t st) {
+  switch (form) {
+    case QFS_FORM_INT32: return FormLauncher<0>::fused(prm, grid, smem, st);
+    default: return FormLauncher<1>::fused(prm, grid, smem, st);
+  }
+}
+
+cudaError_t form_debug(int form, int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *A, uint32_t *B,
+                       uint32_t *status, DebugPtrs dbg, cudaStream_t st) {
+  switch (form) {
+    case QFS_FORM_INT32: return FormLauncher<0>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
+    default: return FormLauncher<1>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
+  }
+}
+
+bool form_supported(int form) { return form == QFS_FORM_INT32 || form == QFS_FORM_DP4A; }
+
+// Default workspace budget: a quarter of device memory.
+size_t default_budget(const DeviceState &S) { return S.total_mem / 4; }
+
+struct Plan {
+  int grid = 0;
+  size_t smem = 0;
+  size_t ws_words = 0;
+};
+
+int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_options_t *opts, Plan &plan) {
+  plan.smem = smem_bytes_for(max_p);
+  plan.ws_words = (size_t)padded_words(4 * max_p * (max_p - 1));
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
+  if (per_sm == 0) {
+    int blocks = 0;
+    cudaError_t e = form_occupancy(form, &blocks, plan.smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    per_sm = std::max(1, blocks);
+  }
+  int64_t grid = (int64_t)S.sms * per_sm;
+  if (opts && opts->max_ctas > 0) grid = std::min<int64_t>(grid, opts->max_ctas);
+  const size_t per_cta = 2 * plan.ws_words * sizeof(uint32_t);
+  const size_t budget = opts && opts->workspace_budget ? opts->workspace_budget : default_budget(S);
+  grid = std::min<int64_t>(grid, (int64_t)(budget / per_cta));
+  grid = std::min<int64_t>(grid, n_items);
+  if (grid < 1) return QFS_ERR_NO_MEMORY;
+  plan.grid = (int)grid;
+  return ensure_workspace(S, (size_t)grid * per_cta);
+}
+
+}  // namespace
+
+}  // namespace qfs
+
+using namespace qfs;
+
+extern "C" {
+
+const char *qfs_strerror(int status) {
+  switch (status) {
+    case QFS_OK: return "ok";
+    case QFS_ERR_INVALID_P: return "p must be one of 3, 5, 7, 11, 13";
+    case QFS_ERR_INVALID_MAX_H: return "max_h must lie in [1, 10]";
+    case QFS_ERR_INVALID_N: return "invalid quartic or group count";
+    case QFS_ERR_NULL: return "a required pointer is NULL";
+    case QFS_ERR_NO_MEMORY: return "not enough device memory for the workspace";
+    case QFS_ERR_CUDA: return "a CUDA runtime call failed";
+    case QFS_ERR_FORM: return "unknown or unsupported arithmetic form or engine";
+    case QFS_ERR_DEVICE: return "the current device is not an sm_103 GPU";
+    case QFS_ERR_CHECK: return "a device-side consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+int qfs_last_cuda_error(void) { return g_last_cuda; }
+
+int qfs_set_default_form(int form) {
+  if (!form_supported(form)) return QFS_ERR_FORM;
+  g_default_form = form;
+  return QFS_OK;
+}
+
+int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, const qfs_options_t *opts,
+                         cudaStream_t stream) {
+  if (n_groups < 1 || n_groups > QFS_MAX_GROUPS) return QFS_ERR_INVALID_N;
+  if (!groups) return QFS_ERR_NULL;
+  if (max_h < 1 || max_h > 10) return QFS_ERR_INVALID_MAX_H;
+  int64_t n_items = 0;
+  int max_p = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    const qfs_group_t &g = groups[i];
+    if (!valid_p(g.p)) return QFS_ERR_INVALID_P;
+    if (g.n < 0) return QFS_ERR_INVALID_N;
+    if (g.n > 0 && (!g.coeffs || !g.heights_out)) return QFS_ERR_NULL;
+    n_items += g.n;
+    if (g.n > 0) max_p = std::max(max_p, g.p);
+  }
+  int form = opts && opts->form >= 0 ? opts->form : g_default_form;
+  int engine = opts && opts->engine >= 0 ? opts->engine : QFS_ENGINE_FUSED;
+  if (!form_supported(form) || engine != QFS_ENGINE_FUSED) return QFS_ERR_FORM;
+  if (n_items == 0) return QFS_OK;
+
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+
+  // Largest p first: the heaviest quartics start early, which shortens the tail of the persistent launch.
+  std::vector<int> order(n_groups);
+  for (int i = 0; i < n_groups; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return groups[a].p > groups[b].p; });
+  FusedParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  int k = 0;
+  int64_t begin = 0;
+  for (int oi = 0; oi < n_groups; ++oi) {
+    const qfs_group_t &g = groups[order[oi]];
+    if (g.n == 0) continue;
+    prm.g[k].p = g.p;
+    prm.g[k].n = g.n;
+    prm.g[k].coeffs = g.coeffs;
+    prm.g[k].heights = g.heights_out;
+    prm.g[k].item_begin = begin;
+    begin += g.n;
+    ++k;
+  }
+  prm.n_groups = k;
+  prm.n_items = n_items;
+  prm.max_h = max_h;
+  prm.sw_len = 4 * max_p * (max_p - 1) + 2;
+
+  Plan plan;
+  rc = make_plan(*S, form, max_p, n_items, opts, plan);
+  if (rc) return rc;
+  prm.counter = reinterpret_cast<unsigned long long *>(S->ctrl);
+  prm.status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
+  prm.ws = reinterpret_cast<uint32_t *>(S->ws);
+  prm.ws_words = plan.ws_words;
+  cudaError_t e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = form_fused(form, prm, plan.grid, plan.smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return QFS_OK;
+}
+
+int qfs_heights_multi(int n_groups, const qfs_group_t *groups, int max_h, cudaStream_t stream) {
+  return qfs_heights_multi_ex(n_groups, groups, max_h, nullptr, stream);
+}
+
+int qfs_heights(int p, int64_t n, const uint8_t *coeffs, int max_h, int8_t *heights_out, cudaStream_t stream) {
+  qfs_group_t g;
+  g.p = p;
+  g.n = n;
+  g.coeffs = coeffs;
+  g.heights_out = heights_out;
+  return qfs_heights_multi_ex(1, &g, max_h, nullptr, stream);
+}
+
+int qfs_plan_prepare(int p, int64_t n_hint) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  Plan plan;
+  int64_t n = n_hint > 0 ? n_hint : (int64_t)1 << 40;
+  for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A}) {
+    rc = make_plan(*S, form, p, n, nullptr, plan);
+    if (rc) return rc;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? QFS_OK : cuda_fail(e);
+}
+
+int qfs_shutdown(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  int rc = QFS_OK;
+  for (int d = 0; d < kMaxDevices; ++d) {
+    DeviceState &S = g_dev[d];
+    if (!S.init) continue;
+    if (cudaSetDevice(d) != cudaSuccess) { rc = QFS_ERR_CUDA; continue; }
+    if (S.ws && cudaFree(S.ws) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.ctrl && cudaFree(S.ctrl) != cudaSuccess) rc = QFS_ERR_CUDA;
+    S = DeviceState();
+  }
+  cudaSetDevice(cur);
+  return rc;
+}
+
+int qfs_read_status(uint32_t *status_out) {
+  if (!status_out) return QFS_ERR_NULL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, reinterpret_cast<char *>(S->ctrl) + 8, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemset(reinterpret_cast<char *>(S->ctrl) + 8, 0, 4);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *status_out = v;
+  return QFS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------- parity hook
+namespace qfs {
+namespace {
+
+__global__ void unpad_kernel(const uint32_t *__restrict__ padded, int m, const int *__restrict__ SWg,
+                             int32_t *__restrict__ out) {
+  const int n = tet(m + 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int u, s, t;
+    decode_packed(i, u, s, t);
+    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(padded);
+    out[i] = bytes[4 * ((size_t)SWg[u] + colw(s)) + t];
+  }
+}
+
+}  // namespace
+}  // namespace qfs
+
+extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
+                                int32_t *delta_out, int32_t *iters_out, int8_t *height_out) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (max_h < 1 || max_h > 10) return QFS_ERR_INVALID_MAX_H;
+  if (!coeffs || !height_out) return QFS_ERR_NULL;
+  if (!form_supported(form)) return QFS_ERR_FORM;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  const int d = 4 * (p - 1), D = 4 * p * (p - 1);
+  const size_t words = (size_t)padded_words(D);
+  const size_t ld = (size_t)tet(d + 1);
+  uint32_t *A = nullptr, *B = nullptr, *Gp = nullptr, *Dp = nullptr;
+  int32_t *gtmp = nullptr, *itmp = nullptr;
+  int *SWg = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](cudaError_t err) {
+    cudaFree(A); cudaFree(B); cudaFree(Gp); cudaFree(Dp); cudaFree(gtmp); cudaFree(itmp); cudaFree(SWg);
+    return cuda_fail(err);
+  };
+  if ((e = cudaMalloc(&A, words * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&B, words * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&Gp, words * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&Dp, words * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&gtmp, ld * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&itmp, ld * 4 * 9)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&SWg, sizeof(int) * (D + 3))) != cudaSuccess) return fail(e);
+  cudaMemset(Gp, 0, words * 4);
+  cudaMemset(Dp, 0, words * 4);
+  cudaMemset(gtmp, 0, ld * 4);
+  cudaMemset(itmp, 0, ld * 4 * 9);
+  std::vector<int> sw(D + 3);
+  for (int u = 0; u < D + 3; ++u) sw[u] = (int)host_sw(u);
+  cudaMemcpy(SWg, sw.data(), sizeof(int) * (D + 3), cudaMemcpyHostToDevice);
+  DebugPtrs dbg{Gp, Dp, gtmp, itmp};
+  uint32_t *status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
+  if ((e = form_debug(form, p, coeffs, max_h, height_out, A, B, status, dbg, 0)) != cudaSuccess) return fail(e);
+  if (G_out) unpad_kernel<<<256, 256>>>(Gp, D, SWg, G_out);
+  if (delta_out) unpad_kernel<<<256, 256>>>(Dp, D, SWg, delta_out);
+  if (g_out) cudaMemcpy(g_out, gtmp, ld * 4, cudaMemcpyDeviceToDevice);
+  if (iters_out && max_h > 1) cudaMemcpy(iters_out, itmp, ld * 4 * (max_h - 1), cudaMemcpyDeviceToDevice);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
+  cudaFree(A); cudaFree(B); cudaFree(Gp); cudaFree(Dp); cudaFree(gtmp); cudaFree(itmp); cudaFree(SWg);
+  return QFS_OK;
+}

@@ -1,0 +1,67 @@
+// Kernel entry points of one arithmetic form (instantiated once per form in its own translation unit).
+#pragma once
+#include <cuda_runtime.h>
+#include "qfs_engine.cuh"
+
+namespace qfs {
+
+// Persistent launch: every CTA pulls quartics from a global atomic queue until the queue is empty.
+template <int FORM>
+__global__ void __launch_bounds__(kThreads) fused_kernel(FusedParams prm) {
+  fused_body<FORM>(prm);
+}
+
+// One quartic with every intermediate array written out (kernel-level parity hook).
+template <int P, int FORM>
+__global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,
+                                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+  uint8_t *gs = smem_raw + sizeof(Smem);
+  uint8_t *gn = gs + Prime<P>::ld;
+  build_sw(sm.SW, Prime<P>::D + 2);
+  __syncthreads();
+  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, bufA, bufB, status, dbg);
+  if (threadIdx.x == 0) *h_out = (int8_t)h;
+}
+
+// Host-side launchers (defined in qfs_form_<name>.cu).
+template <int FORM>
+struct FormLauncher {
+  static cudaError_t fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st);
+  static cudaError_t occupancy(int *blocks_per_sm, size_t smem);
+  static cudaError_t debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA, uint32_t *bufB,
+                           uint32_t *status, DebugPtrs dbg, cudaStream_t st);
+};
+
+#define QFS_DEFINE_FORM_LAUNCHER(FORM)                                                                        \
+  template <>                                                                                                 \
+  cudaError_t FormLauncher<FORM>::fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st) {     \
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                         (int)smem);                                                          \
+    if (e != cudaSuccess) return e;                                                                           \
+    fused_kernel<FORM><<<grid, kThreads, smem, st>>>(prm);                                                    \
+    return cudaGetLastError();                                                                                \
+  }                                                                                                           \
+  template <>                                                                                                 \
+  cudaError_t FormLauncher<FORM>::occupancy(int *blocks_per_sm, size_t smem) {                                \
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                         (int)smem);                                                          \
+    if (e != cudaSuccess) return e;                                                                           \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<FORM>, kThreads, smem);  \
+  }                                                                                                           \
+  template <>                                                                                                 \
+  cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
+                                        uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st) {   \
+    const size_t smem = smem_bytes_for(p);                                                                    \
+    switch (p) {                                                                                              \
+      case 3: debug_kernel<3, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+      case 5: debug_kernel<5, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+      case 7: debug_kernel<7, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+      case 11: debug_kernel<11, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+      default: debug_kernel<13, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+    }                                                                                                         \
+    return cudaGetLastError();                                                                                \
+  }
+
+}  // namespace qfs

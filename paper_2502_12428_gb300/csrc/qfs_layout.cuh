@@ -1,0 +1,97 @@
+// Coefficient layouts shared by every libqfs kernel.
+//
+// A homogeneous form of degree m in x1..x4 is addressed by (u, s, t) = (e2+e3+e4, e3+e4, e4) with
+// 0 <= t <= s <= u <= m (the exponent of x1 is m - u).  Products of monomials add (u, s, t), so a product of
+// forms is a 3-D convolution over this cone and the degree only bounds u.
+//
+// Packed layout ("descending lex"): index = tet(u) + tri(s) + t, with tet(u) = C(u+2,3), tri(s) = C(s+1,2).
+// It enumerates the monomials with x1's exponent descending, then x2's, then x3's -- the order in which the paper
+// prints quartics (Figures 4-7) and the order of every array that crosses the C ABI.  A form of degree m has
+// C(m+3,3) = tet(m+1) entries (the paper's l_d, Sec. 4).
+//
+// Padded layout (device workspaces): the same order, but every column (u, s) -- the s+1 entries t = 0..s -- starts
+// on a 4-byte boundary and occupies W(s) = s/4 + 1 words of four one-byte residues; padding bytes are zero.
+// Word offset of column (u, s) = SW[u] + colw(s), where colw(s) = sum_{s' < s} W(s') = (q+1)(2q+r) for s = 4q+r
+// and SW[u] = sum_{v < u} colw(v+1).  SW does not depend on m; a degree-m form uses words [0, SW[m+1]).
+#pragma once
+#include <cstdint>
+
+namespace qfs {
+
+__host__ __device__ constexpr int tet(int u) { return u * (u + 1) * (u + 2) / 6; }
+__host__ __device__ constexpr int tri(int s) { return s * (s + 1) / 2; }
+__host__ __device__ constexpr int colw(int s) { return ((s >> 2) + 1) * (2 * (s >> 2) + (s & 3)); }
+__host__ __device__ constexpr int n_monomials(int m) { return tet(m + 1); }
+
+// Largest prime the engine accepts and the derived sizes.
+constexpr int kMaxP = 13;
+constexpr int kMaxD = 4 * kMaxP * (kMaxP - 1);   // 624
+constexpr int kSWLen = kMaxD + 6;                // SW[0 .. kMaxD+5]
+
+template <int P>
+struct Prime {
+  static constexpr int p = P;
+  static constexpr int p2 = P * P;
+  static constexpr int d = 4 * (P - 1);          // degree of g = f^(p-1)
+  static constexpr int D = 4 * P * (P - 1);      // degree of Delta_1(f^(p-1))
+  static constexpr int ld = tet(d + 1);          // C(4p-1, 3)
+  static constexpr int lD = tet(D + 1);
+  // witness monomial (x1 x2 x3 x4)^(p-1) in degree d: (u, s, t) = (3(p-1), 2(p-1), p-1)
+  static constexpr int wu = 3 * (P - 1), ws = 2 * (P - 1), wt = P - 1;
+  static constexpr int witness = tet(wu) + tri(ws) + wt;
+};
+
+// SW table on the host (sizes, admission) -- same recurrence as the device copy.
+inline int64_t host_sw(int u) {
+  int64_t acc = 0;
+  for (int v = 0; v < u; ++v) acc += colw(v + 1);
+  return acc;
+}
+inline int64_t padded_words(int m) { return host_sw(m + 1); }
+
+#if defined(__CUDACC__)
+// Fill SW[0 .. n-1] in shared memory (n <= kSWLen); callers __syncthreads() afterwards.
+__device__ __forceinline__ void build_sw(int *SW, int n) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int u = 0; u < n; ++u) {
+      SW[u] = acc;
+      acc += colw(u + 1);
+    }
+  }
+}
+
+// Flat word index k of a degree-m padded form -> (u, s, w): column (u, s), word w (entries t = 4w .. 4w+3).
+__device__ __forceinline__ void decode_word(int k, int m, const int *SW, int &u, int &s, int &w) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (SW[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  u = lo;
+  int kk = k - SW[u];
+  int q = (int)((sqrtf(2.0f * (float)kk + 1.0f) - 1.0f) * 0.5f);
+  while (2 * (q + 1) * (q + 2) <= kk) ++q;
+  while (q > 0 && 2 * q * (q + 1) > kk) --q;
+  int rem = kk - 2 * q * (q + 1);
+  int r = rem / (q + 1);
+  w = rem - r * (q + 1);
+  s = 4 * q + r;
+}
+
+// Packed index i of a form (degree <= kMaxD) -> (u, s, t).
+__device__ __forceinline__ void decode_packed(int i, int &u, int &s, int &t) {
+  int uu = (int)cbrtf(6.0f * (float)i);
+  while (uu > 0 && tet(uu) > i) --uu;
+  while (tet(uu + 1) <= i) ++uu;
+  int rem = i - tet(uu);
+  int ss = (int)((sqrtf(8.0f * (float)rem + 1.0f) - 1.0f) * 0.5f);
+  while (ss > 0 && tri(ss) > rem) --ss;
+  while (tri(ss + 1) <= rem) ++ss;
+  u = uu;
+  s = ss;
+  t = rem - tri(ss);
+}
+#endif
+
+}  // namespace qfs

@@ -1,0 +1,186 @@
+"""Python binding of libqfs (include/qfs.h): argument marshalling only, every step runs in the CUDA library.
+
+Tensors are PyTorch CUDA tensors; the binding passes their data pointers and the current CUDA stream.  There is
+no CPU fallback: if the library is not built, or no CUDA device is present, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqfs.so")
+
+OK = 0
+FORM_INT32, FORM_DP4A, FORM_INT8TC = 0, 1, 2
+ENGINE_FUSED, ENGINE_STAGED = 0, 1
+FORMS = {"int32": FORM_INT32, "dp4a": FORM_DP4A, "int8tc": FORM_INT8TC}
+ENGINES = {"fused": ENGINE_FUSED, "staged": ENGINE_STAGED}
+MAX_GROUPS = 8
+PRIMES = (3, 5, 7, 11, 13)
+
+
+class QfsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib().qfs_strerror(status).decode() if _LIB is not None else f"status {status}"
+        if status == 6 and _LIB is not None:
+            msg += f" (cudaError {_LIB.qfs_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+class Group(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("n", ctypes.c_int64), ("coeffs", ctypes.c_void_p),
+                ("heights_out", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("engine", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("max_ctas", ctypes.c_int), ("workspace_budget", ctypes.c_size_t)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libqfs is not built ({LIB_PATH} missing): run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.qfs_heights.argtypes = [c_int, i64, vp, c_int, vp, vp]
+        L.qfs_heights_multi.argtypes = [c_int, ctypes.POINTER(Group), c_int, vp]
+        L.qfs_heights_multi_ex.argtypes = [c_int, ctypes.POINTER(Group), c_int, ctypes.POINTER(Options), vp]
+        L.qfs_set_default_form.argtypes = [c_int]
+        L.qfs_plan_prepare.argtypes = [c_int, i64]
+        L.qfs_shutdown.argtypes = []
+        L.qfs_read_status.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+        L.qfs_strerror.argtypes = [c_int]
+        L.qfs_strerror.restype = ctypes.c_char_p
+        L.qfs_last_cuda_error.argtypes = []
+        L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
+        for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
+                     "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_last_cuda_error",
+                     "qfs_debug_stages"):
+            getattr(L, name).restype = c_int
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded ctypes library (loads it on first use)."""
+    return _lib()
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise QfsError(rc, where)
+
+
+def _need_cuda(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _options(form, engine, ctas_per_sm, max_ctas, workspace_budget):
+    o = Options()
+    o.form = FORMS[form] if isinstance(form, str) else (-1 if form is None else int(form))
+    o.engine = ENGINES[engine] if isinstance(engine, str) else (-1 if engine is None else int(engine))
+    o.ctas_per_sm = int(ctas_per_sm)
+    o.max_ctas = int(max_ctas)
+    o.workspace_budget = int(workspace_budget)
+    return o
+
+
+def heights(p, coeffs, max_h=10, out=None, stream=None, form=None, engine=None, ctas_per_sm=0, max_ctas=0,
+            workspace_budget=0):
+    """Heights of the quartics in `coeffs` (CUDA uint8 tensor, n x 35, descending lex) over F_p.
+
+    Returns an int8 CUDA tensor of n codes (1..max_h height, 0 infinity, -1 invalid row).  Asynchronous on the
+    current stream (or `stream`).
+    """
+    _need_cuda(coeffs, torch.uint8, "coeffs")
+    if coeffs.dim() != 2 or coeffs.shape[1] != 35:
+        raise ValueError("coeffs must have shape (n, 35)")
+    n = coeffs.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.int8, device=coeffs.device)
+    _need_cuda(out, torch.int8, "out")
+    return heights_multi([(p, coeffs, out)], max_h, stream, form, engine, ctas_per_sm, max_ctas,
+                         workspace_budget)[0]
+
+
+def heights_multi(groups, max_h=10, stream=None, form=None, engine=None, ctas_per_sm=0, max_ctas=0,
+                  workspace_budget=0):
+    """One launch over several (p, coeffs, out) batches; `out` may be None.  Returns the list of outputs."""
+    if not 1 <= len(groups) <= MAX_GROUPS:
+        raise ValueError(f"between 1 and {MAX_GROUPS} groups")
+    arr = (Group * len(groups))()
+    outs = []
+    for i, (p, coeffs, out) in enumerate(groups):
+        _need_cuda(coeffs, torch.uint8, "coeffs")
+        if coeffs.dim() != 2 or coeffs.shape[1] != 35:
+            raise ValueError("coeffs must have shape (n, 35)")
+        if out is None:
+            out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=coeffs.device)
+        _need_cuda(out, torch.int8, "out")
+        if out.numel() != coeffs.shape[0]:
+            raise ValueError("out must have one entry per quartic")
+        arr[i].p, arr[i].n = int(p), int(coeffs.shape[0])
+        arr[i].coeffs, arr[i].heights_out = coeffs.data_ptr(), out.data_ptr()
+        outs.append(out)
+    opts = _options(form, engine, ctas_per_sm, max_ctas, workspace_budget)
+    rc = _lib().qfs_heights_multi_ex(len(groups), arr, int(max_h), ctypes.byref(opts), _stream(stream))
+    _check(rc, "qfs_heights_multi_ex")
+    return outs
+
+
+def set_default_form(form):
+    _check(_lib().qfs_set_default_form(FORMS[form] if isinstance(form, str) else int(form)), "qfs_set_default_form")
+
+
+def plan_prepare(p, n_hint=0):
+    _check(_lib().qfs_plan_prepare(int(p), int(n_hint)), "qfs_plan_prepare")
+
+
+def shutdown():
+    _check(_lib().qfs_shutdown(), "qfs_shutdown")
+
+
+def read_status():
+    v = ctypes.c_uint32(0)
+    _check(_lib().qfs_read_status(ctypes.byref(v)), "qfs_read_status")
+    return v.value
+
+
+def debug_stages(p, coeffs, max_h=10, form="dp4a"):
+    """Runs the device pipeline on one quartic and returns every intermediate array (int32 CUDA tensors,
+    descending lex): dict(h, g, G, delta, iters).  Synchronous; for parity tests."""
+    _need_cuda(coeffs, torch.uint8, "coeffs")
+    coeffs = coeffs.reshape(35).contiguous()
+    dev = coeffs.device
+    ld = (4 * p - 1) * (4 * p - 2) * (4 * p - 3) // 6
+    D = 4 * p * (p - 1)
+    lD = (D + 3) * (D + 2) * (D + 1) // 6
+    g = torch.zeros(ld, dtype=torch.int32, device=dev)
+    G = torch.zeros(lD, dtype=torch.int32, device=dev)
+    delta = torch.zeros(lD, dtype=torch.int32, device=dev)
+    iters = torch.zeros(max(max_h - 1, 1), ld, dtype=torch.int32, device=dev)
+    h = torch.zeros(1, dtype=torch.int8, device=dev)
+    torch.cuda.synchronize(dev)
+    rc = _lib().qfs_debug_stages(int(p), coeffs.data_ptr(), int(max_h), FORMS[form] if isinstance(form, str)
+                                 else int(form), g.data_ptr(), G.data_ptr(), delta.data_ptr(), iters.data_ptr(),
+                                 h.data_ptr())
+    _check(rc, "qfs_debug_stages")
+    return dict(h=int(h.item()), g=g, G=G, delta=delta, iters=iters)

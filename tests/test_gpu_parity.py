@@ -1,0 +1,226 @@
+"""CUDA path vs the CPU oracle: stage arrays element by element, heights bit-exact, full-size sampled checks.
+
+Every test here calls libqfs through its C ABI (via the ctypes binding) on cuda:0.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import example_quartics
+from paper_2502_12428_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CORE_FORMS = ["int32", "dp4a"]
+
+
+@pytest.fixture(scope="session")
+def qfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_12428_gb300 import build
+    build.build()
+    import paper_2502_12428_gb300.qfs as q
+    return q
+
+
+def dev_tensor(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def gpu_heights(qfs, p, f, **kw):
+    return qfs.heights(p, dev_tensor(f), **kw).cpu().numpy()
+
+
+def find_rows(p, n, seed, want, count, gen=inputs.dense):
+    f = gen(p, n, seed)
+    h = oracle.heights(p, f)
+    idx = [i for i in range(n) if want(h[i])][:count]
+    return f[idx], h[idx]
+
+
+# ------------------------------------------------------------------------------------- stage arrays
+def check_stages(qfs, p, f, form, max_h=10):
+    ref = oracle.stage_arrays_a(p, f, max_h=max_h)
+    got = qfs.debug_stages(p, dev_tensor(f), max_h=max_h, form=form)
+    assert got["h"] == ref["h"]
+    assert np.array_equal(got["g"].cpu().numpy(), ref["g"]), "f^(p-1) mod p"
+    if ref["h"] != 1:
+        assert np.array_equal(got["G"].cpu().numpy(), ref["D"]), "lift(g)^p mod p^2"
+        assert np.array_equal(got["delta"].cpu().numpy(), ref["delta"]), "Delta_1(f^(p-1))"
+        rows = ref["iters"].shape[0]
+        assert np.array_equal(got["iters"].cpu().numpy()[:rows], ref["iters"]), "theta iterates"
+    return ref["h"]
+
+
+@pytest.mark.parametrize("form", CORE_FORMS)
+def test_stages_p3(qfs, form):
+    f = np.concatenate([inputs.dense(3, 10, 301), inputs.sparse(3, 4, 302), inputs.fermat()[None]])
+    hs = [check_stages(qfs, 3, row, form) for row in f]
+    assert any(h != 1 for h in hs)
+
+
+@pytest.mark.parametrize("form", CORE_FORMS)
+def test_stages_p5(qfs, form):
+    f, h = find_rows(5, 400, 501, lambda x: x >= 2 or x == 0, 5)
+    ex = [r[3] for r in example_quartics() if r[0] == 5 and r[1] in (1, 3, 0)]
+    for row in list(f) + ex:
+        check_stages(qfs, 5, row, form)
+
+
+@pytest.mark.slow
+def test_stages_p7(qfs):
+    row = next(r[3] for r in example_quartics() if r[0] == 7 and r[1] == 2)
+    ref = oracle.stage_arrays_a(7, row)
+    for form in CORE_FORMS:
+        got = qfs.debug_stages(7, dev_tensor(row), form=form)
+        assert got["h"] == ref["h"] == 2
+        assert np.array_equal(got["g"].cpu().numpy(), ref["g"])
+        assert np.array_equal(got["G"].cpu().numpy(), ref["D"])
+        assert np.array_equal(got["delta"].cpu().numpy(), ref["delta"])
+        assert np.array_equal(got["iters"].cpu().numpy()[:1], ref["iters"])
+
+
+# ------------------------------------------------------------------------------------- heights, small sets
+@pytest.mark.parametrize("form", CORE_FORMS)
+def test_heights_p3_64_plus_fermat(qfs, form):
+    f = np.concatenate([inputs.dense(3, 64, inputs.config_seed(1)), inputs.fermat()[None]])
+    want = oracle.heights(3, f, route=oracle.ROUTE_A)
+    got = gpu_heights(qfs, 3, f, form=form)
+    assert np.array_equal(got, want)
+    assert got[-1] == 0  # Fermat quartic at p = 3: infinity
+
+
+@pytest.mark.parametrize("form", CORE_FORMS)
+def test_heights_paper_examples(qfs, form):
+    rows = example_quartics()
+    for p in (5, 7, 11, 13):
+        sel = [r for r in rows if r[0] == p]
+        f = np.stack([r[3] for r in sel])
+        want = np.array([r[1] for r in sel], np.int8)
+        assert np.array_equal(gpu_heights(qfs, p, f, form=form), want), f"p={p}"
+
+
+@pytest.mark.parametrize("p,n", [(3, 2000), (5, 4096), (7, 1024), (11, 48)])
+def test_heights_random_dense_and_sparse(qfs, p, n):
+    f = np.concatenate([inputs.dense(p, n, 900 + p), inputs.sparse(p, n, 950 + p)])
+    want = oracle.heights(p, f)
+    for form in CORE_FORMS:
+        assert np.array_equal(gpu_heights(qfs, p, f, form=form), want), form
+
+
+def test_route_a_subset_p5(qfs):
+    f = inputs.dense(5, 300, 1234)
+    want = oracle.heights(5, f, route=oracle.ROUTE_A)
+    assert np.array_equal(gpu_heights(qfs, 5, f), want)
+
+
+# ------------------------------------------------------------------------------------- full sizes, sampled
+def sampled_check(qfs, p, f, got, n_uniform=1500, seed=0):
+    n = f.shape[0]
+    rng = np.random.default_rng(seed)
+    idx = set(rng.choice(n, size=min(n_uniform, n), replace=False).tolist())
+    idx |= set(np.nonzero((got >= 3) | (got == 0))[0][:4000].tolist())  # every rare outcome up to a cap
+    idx = np.array(sorted(idx))
+    want = oracle.heights(p, f[idx])
+    assert np.array_equal(got[idx], want)
+    return idx.size
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg", [2, 4])
+def test_full_size_dense(qfs, cfg):
+    (p, n, kind), = inputs.CONFIG_SIZES[cfg]
+    f = inputs.dense(p, n, inputs.config_seed(cfg))
+    ft = dev_tensor(f)
+    got = {form: qfs.heights(p, ft, form=form).cpu().numpy() for form in CORE_FORMS}
+    assert np.array_equal(got["int32"], got["dp4a"])
+    h = got["dp4a"]
+    assert h.min() >= 0 and h.max() <= 10
+    checked = sampled_check(qfs, p, f, h, seed=cfg)
+    assert checked > 1000
+    # the h >= 2 fraction sits near the 1/p of the paper's heuristic (Sec. 7), wide band
+    frac = float((h != 1).mean())
+    assert abs(frac - 1 / p) < 0.05
+
+
+@pytest.mark.slow
+def test_full_size_sparse_p5(qfs):
+    (p, n, kind), = inputs.CONFIG_SIZES[3]
+    f = inputs.sparse(p, n, inputs.config_seed(3))
+    h = gpu_heights(qfs, p, f)
+    assert h.min() >= 0 and h.max() <= 10
+    sampled_check(qfs, p, f, h, n_uniform=3000, seed=3)
+
+
+# ------------------------------------------------------------------------------------- mixed primes in one launch
+def test_multi_group_mixed_and_pgl4(qfs):
+    groups, wants, pairs = [], [], []
+    for p, n in [(5, 2048), (7, 1024), (11, 32)]:
+        f = inputs.dense(p, n, 7700 + p)
+        A = inputs.pgl4_matrices(p, n, 7800 + p)
+        g = inputs.substitute(f, A, p)
+        both = np.concatenate([f, g])
+        groups.append((p, dev_tensor(both), None))
+        wants.append(oracle.heights(p, both))
+        pairs.append(n)
+    outs = [o.cpu().numpy() for o in qfs.heights_multi(groups)]
+    for out, want, n in zip(outs, wants, pairs):
+        assert np.array_equal(out, want)
+        assert np.array_equal(out[:n], out[n:])  # PGL_4 invariance of the height
+    # one launch equals separate launches
+    for (p, t, _), out in zip(groups, outs):
+        assert np.array_equal(qfs.heights(p, t).cpu().numpy(), out)
+
+
+# ------------------------------------------------------------------------------------- edge cases and errors
+def test_edge_cases(qfs):
+    p = 5
+    assert qfs.heights(p, torch.zeros(0, 35, dtype=torch.uint8, device="cuda:0")).numel() == 0
+    f = inputs.dense(p, 1000, 4242)
+    bad = f.copy()
+    bad[3, 0] = p
+    bad[500, 34] = 255
+    got = gpu_heights(qfs, p, bad)
+    want = oracle.heights(p, f)
+    assert got[3] == -1 and got[500] == -1
+    keep = np.ones(1000, bool)
+    keep[[3, 500]] = False
+    assert np.array_equal(got[keep], want[keep])
+    for n in (1, 7, 153):
+        assert np.array_equal(gpu_heights(qfs, p, f[:n]), want[:n])
+    # max_h caps: with max_h = 1 only the Fedder test runs
+    h1 = gpu_heights(qfs, p, f, max_h=1)
+    assert np.array_equal(h1, np.where(want == 1, 1, 0).astype(np.int8))
+    h3 = gpu_heights(qfs, p, f, max_h=3)
+    assert np.array_equal(h3, np.where((want >= 1) & (want <= 3), want, 0).astype(np.int8))
+    # the all-zero form: f^(p-1) = 0, every iterate is zero -> infinity
+    assert gpu_heights(qfs, p, np.zeros((1, 35), np.uint8))[0] == oracle.height_a(p, np.zeros(35, np.uint8)) == 0
+
+
+def test_error_codes(qfs):
+    t = dev_tensor(inputs.dense(5, 4, 1))
+    with pytest.raises(qfs.QfsError) as e:
+        qfs.heights(4, t)
+    assert e.value.status == 1
+    with pytest.raises(qfs.QfsError) as e:
+        qfs.heights(5, t, max_h=11)
+    assert e.value.status == 2
+    with pytest.raises(qfs.QfsError) as e:
+        qfs.heights(5, t, form=9)
+    assert e.value.status == 7
+
+
+def test_determinism_across_cta_counts(qfs):
+    p = 7
+    f = inputs.dense(p, 3000, 5151)
+    t = dev_tensor(f)
+    ref = qfs.heights(p, t).cpu().numpy()
+    for cap in (1, 3, 37):
+        assert np.array_equal(qfs.heights(p, t, max_ctas=cap).cpu().numpy(), ref)
+    assert np.array_equal(ref, oracle.heights(p, f))
+
+
+def test_device_status_clean(qfs):
+    assert qfs.read_status() == 0
