@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Throughput of quasi-F-split height classification on GB300: quartics per second, bit-exact.
+
+One step = one pass of the whole hot path (f^(p-1), Fedder test, power chain to f^(p(p-1)) mod p^2, Delta_1,
+theta iterations with early exit) over one batch of seeded random quartics, the paper's own workload (Sec. 7.1):
+coefficients uniform in F_p^35.  The headline workload is p = 7, 262,144 quartics; the same run also times
+p = 5, 65,536 quartics and every arithmetic form.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--form dp4a|int32|int8tc]
+
+Multi-GPU (torchrun, one rank per GPU): every rank classifies its own n quartics (rows rank*n .. rank*n+n-1 of
+the same generator); there is no data-path collective, the ranks only meet for the barrier and the max-time
+reduction ("scaling": "weak").  --impl reference times the CPU oracle (the literal Algorithms 1-3) on the host.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_12428_gb300 import inputs  # noqa: E402
+
+METRIC = "quartics/sec height-classified at p=5,7 (1 GB300), bit-exact; int8-TC vs int32 form"
+HEADLINE_CFG = 4        # p = 7, 262,144 dense quartics
+SECOND_CFG = 2          # p = 5, 65,536 dense quartics
+PAPER_P7_RATE = 185.0   # surfaces/s at p = 7, paper Sec. 7.2 (2080 Ti; context, other hardware)
+SMS, SM_MAX_MHZ = 152, 2070.0
+# integer lanes per SM per clock (IMAD and IDP4A pipes: 4 SMSPs x 16 lanes); a DP4A lane does 4 MACs
+LANES = {"int32": 64, "dp4a": 64 * 4, "int8tc": 64 * 4}
+
+
+# ----------------------------------------------------------------------------------------------- work counts
+def n_mon(d):
+    return (d + 3) * (d + 2) * (d + 1) // 6 if d >= 0 else 0
+
+
+def chain_macs(p, k_from, k_to):
+    """MACs of f^(k+1) = f^k * f for k in [k_from, k_to]: every term of f^k meets each of f's 35 terms once."""
+    return sum(n_mon(4 * k) * 35 for k in range(k_from, k_to + 1))
+
+
+def theta_nnz(p):
+    """Nonzero entries of the matrix of g -> u(Delta g) on degree-4(p-1) forms: pairs (r, c) whose Delta index
+    p r + (p-1) - c has no negative exponent (Sec. 4, matching monomials)."""
+    d = 4 * (p - 1)
+    mons = np.array([(e1, e2, e3, d - e1 - e2 - e3) for e1 in range(d, -1, -1) for e2 in range(d - e1, -1, -1)
+                     for e3 in range(d - e1 - e2, -1, -1)], np.int64)
+    total = 0
+    for chunk in np.array_split(np.arange(len(mons)), max(1, len(mons) // 256)):
+        e = p * mons[chunk][:, None, :] + (p - 1) - mons[None, :, :]
+        total += int((e >= 0).all(axis=2).sum())
+    return total
+
+
+def algorithmic_macs(p, n, survivors, theta_steps):
+    a2 = chain_macs(p, 1, p - 2)
+    a4 = chain_macs(p, p - 1, p * (p - 1) - 1)
+    return n * a2 + survivors * a4 + theta_steps * theta_nnz(p)
+
+
+# ----------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        mhz = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        if not mhz:
+            return None
+        maxmhz = max(float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": maxmhz, "reasons": reasons, "samples": len(mhz)}
+
+
+# ----------------------------------------------------------------------------------------------- helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2502_12428_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(form, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        data = json.load(fh)
+    ent = data.get(form, {}).get(workload)
+    if not ent or ent.get("kernel_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def config_batch(cfg, rank=0):
+    (p, n, kind), = inputs.CONFIG_SIZES[cfg]
+    seed = inputs.config_seed(cfg)
+    gen = inputs.sparse if kind == "sparse" else inputs.dense
+    return p, n, kind, gen(p, n, seed, row0=rank * n)
+
+
+def workload_name(cfg):
+    (p, n, kind), = inputs.CONFIG_SIZES[cfg]
+    return f"p{p}-{kind}-{n}"
+
+
+# ----------------------------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2502_12428_gb300.qfs as qfs
+    from paper_2502_12428_gb300 import build as qbuild
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    qfs.lib()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(p, coeffs, form, steps, warmup):
+        out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=dev)
+        for _ in range(warmup):
+            qfs.heights(p, coeffs, out=out, form=form)
+        torch.cuda.synchronize()
+        qfs.read_stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)                # L2 flush between timed steps, outside the events
+            ev[i][0].record(stream)
+            qfs.heights(p, coeffs, out=out, form=form)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        per = [a.elapsed_time(b) for a, b in ev]
+        survivors, theta = qfs.read_stats()
+        return out, per, survivors / steps, theta / steps
+
+    result = {}
+    forms = [args.form] + [f for f in ("int32", "dp4a", "int8tc") if f != args.form and f in args.forms]
+    # headline: timed with the clock sampler running
+    p, n, kind, f_np = config_batch(HEADLINE_CFG, rank)
+    coeffs = torch.from_numpy(f_np).to(dev)
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    out, per, surv, theta = timed_steps(p, coeffs, args.form, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    ms_step = max_over_ranks(statistics.mean(per))
+    heights_np = out.cpu().numpy()
+    value = world * n / (ms_step / 1e3)
+    macs = algorithmic_macs(p, n, surv, theta)
+    achieved = 2 * macs / (statistics.mean(per) / 1e3) / 1e12
+    peak = SMS * LANES[args.form] * SM_MAX_MHZ * 1e6 * 2 / 1e12
+    traffic = profiled_traffic(args.form, workload_name(HEADLINE_CFG))
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TOP/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": f"qfs::fused_kernel<{ {'int32': 0, 'dp4a': 1, 'int8tc': 2}[args.form]}>",
+                "ops_per_launch": 2 * macs, "peak_basis": f"{SMS} SMs x {LANES[args.form]} int MAC lanes x "
+                f"{SM_MAX_MHZ:.0f} MHz x 2 ops (nominal; 1 MAC = 2 ops)"}
+
+    forms_out = {args.form: {"value": round(value, 1), "ms_per_step": round(ms_step, 3),
+                             "frac_of_alu_peak": roofline["frac"]}}
+    for form in forms[1:]:
+        try:
+            o2, per2, s2, t2 = timed_steps(p, coeffs, form, max(2, args.steps // 2), args.warmup)
+        except qfs.QfsError as e:
+            forms_out[form] = {"unavailable": str(e)}
+            continue
+        ms2 = max_over_ranks(statistics.mean(per2))
+        pk2 = SMS * LANES[form] * SM_MAX_MHZ * 1e6 * 2 / 1e12
+        ach2 = 2 * algorithmic_macs(p, n, s2, t2) / (statistics.mean(per2) / 1e3) / 1e12
+        forms_out[form] = {"value": round(world * n / (ms2 / 1e3), 1), "ms_per_step": round(ms2, 3),
+                           "frac_of_alu_peak": round(ach2 / pk2, 4),
+                           "bit_exact_vs_headline_form": bool(np.array_equal(o2.cpu().numpy(), heights_np))}
+
+    # second workload (p = 5)
+    p5, n5, kind5, f5 = config_batch(SECOND_CFG, rank)
+    c5 = torch.from_numpy(f5).to(dev)
+    second = {"workload": workload_name(SECOND_CFG)}
+    for form in forms:
+        try:
+            o5, per5, s5, t5 = timed_steps(p5, c5, form, args.steps, args.warmup)
+        except qfs.QfsError as e:
+            second[form] = {"unavailable": str(e)}
+            continue
+        ms5 = max_over_ranks(statistics.mean(per5))
+        second[form] = {"value": round(world * n5 / (ms5 / 1e3), 1), "ms_per_step": round(ms5, 3)}
+
+    # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step
+    host_in = torch.from_numpy(f_np).pin_memory()
+    host_out = torch.empty(n, dtype=torch.int8).pin_memory()
+    dev_in = torch.empty_like(coeffs)
+    dev_out = torch.empty(n, dtype=torch.int8, device=dev)
+    for _ in range(args.warmup):
+        dev_in.copy_(host_in, non_blocking=True)
+        qfs.heights(p, dev_in, out=dev_out, form=args.form)
+        host_out.copy_(dev_out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dev_in.copy_(host_in, non_blocking=True)
+        qfs.heights(p, dev_in, out=dev_out, form=args.form)
+        host_out.copy_(dev_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    assert np.array_equal(host_out.numpy(), heights_np)
+
+    if rank == 0:
+        hist = np.bincount(heights_np.astype(np.int64) + 1, minlength=12)
+        result = {
+            "metric": METRIC, "value": round(value, 1), "unit": "quartics/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": round(value / PAPER_P7_RATE, 1),
+            "vs_baseline_basis": "paper Sec. 7.2: about 185 surfaces/s at p=7 on 2080 Ti GPUs (other hardware)",
+            "dtype": "int8" if args.form != "int32" else "int32", "data": "synthetic",
+            "config": {"workload": workload_name(HEADLINE_CFG), "p": p, "quartics_per_gpu": n,
+                       "coefficients": "uniform in F_7, splitmix64 seed 0x5EED0004", "max_h": 10,
+                       "form": args.form, "engine": "fused persistent", "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "forms": forms_out, "second_workload": second,
+            "heights_histogram": {"invalid": int(hist[0]), "inf": int(hist[1]),
+                                  **{str(h): int(hist[h + 1]) for h in range(1, 11)}},
+            "work_per_step": {"past_height_1": surv, "theta_steps": theta, "algorithmic_macs": macs},
+            "roofline": roofline,
+            "e2e": {"value": round(world * n / (e2e_ms / 1e3), 1), "unit": "quartics/s",
+                    "h2d_bytes_per_step": int(n * 35), "d2h_bytes_per_step": int(n)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(p, f_np, args.cpu_sample)
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(p, f_np, sample):
+    import oracle
+    cores = os.cpu_count() or 1
+    rows = f_np[:sample]
+    t0 = time.perf_counter()
+    oracle.heights(p, rows, route=oracle.ROUTE_A, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": round(sample / dt, 3), "unit": "quartics/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} quartics of the same workload, route A (literal Algorithms 1-3), "
+                      f"{cores} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p, n, kind, f_np = config_batch(HEADLINE_CFG, 0)
+    cores = os.cpu_count() or 1
+    per = []
+    for i in range(args.warmup + args.steps):
+        rows = f_np[(i * args.cpu_sample) % n:][:args.cpu_sample]
+        t0 = time.perf_counter()
+        oracle.heights(p, rows, route=oracle.ROUTE_A, threads=cores)
+        if i >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(per)
+    value = args.cpu_sample / (ms / 1e3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "quartics/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": workload_name(HEADLINE_CFG), "p": p, "max_h": 10,
+                   "sample_per_step": args.cpu_sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": "quartics/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.cpu_sample} quartics of the workload per step, route A"},
+        "e2e": {"value": round(value, 3), "unit": "quartics/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ncu_case(args):
+    """A small fixed launch for profilers: p = 7, the first --ncu-quartics quartics of the headline workload,
+    one warm-up launch and one profiled launch of the fused kernel."""
+    import torch
+    import paper_2502_12428_gb300.qfs as qfs
+    from paper_2502_12428_gb300 import build as qbuild
+    qbuild.build()
+    p, n, kind, f_np = config_batch(HEADLINE_CFG, 0)
+    coeffs = torch.from_numpy(f_np[:args.ncu_quartics]).cuda()
+    for _ in range(2):
+        h = qfs.heights(p, coeffs, form=args.form, max_ctas=args.ncu_ctas)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": workload_name(HEADLINE_CFG), "quartics": args.ncu_quartics, "form": args.form,
+                      "past_height_1": int((h.cpu().numpy() != 1).sum())}))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["dp4a", "int32", "int8tc"], default="dp4a")
+    ap.add_argument("--forms", default="int32,dp4a,int8tc", help="forms timed besides the headline one")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="quartics per oracle run (default 256 for the baseline leg, 128 per reference step)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
+    ap.add_argument("--ncu-quartics", type=int, default=8192)
+    ap.add_argument("--ncu-ctas", type=int, default=0)
+    args = ap.parse_args()
+    args.forms = args.forms.split(",")
+    if args.cpu_sample is None:
+        args.cpu_sample = 128 if args.impl == "reference" else 256
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.ncu_case:
+        run_ncu_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,6 +113,11 @@ int qfs_shutdown(void);
    then clears it.  Synchronises the current device. */
 int qfs_read_status(uint32_t *status_out);
 
+/* Work counters of the current device's launches since the last call: quartics that passed the height-1 test
+   (so ran the full power chain, Delta_1 and at least one theta step unless max_h = 1) and theta steps run in
+   total.  Clears them.  Synchronises the current device.  Used to turn timings into algorithmic work rates. */
+int qfs_read_stats(uint64_t *survivors, uint64_t *theta_steps);
+
 /* Human-readable text for a status code (static storage). */
 const char *qfs_strerror(int status);
 

@@ -220,6 +220,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   if (rc) return rc;
   prm.counter = reinterpret_cast<unsigned long long *>(S->ctrl);
   prm.status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
+  prm.stats = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->ctrl) + 16);
   prm.ws = reinterpret_cast<uint32_t *>(S->ws);
   prm.ws_words = plan.ws_words;
   cudaError_t e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
@@ -273,6 +274,24 @@ int qfs_shutdown(void) {
   }
   cudaSetDevice(cur);
   return rc;
+}
+
+int qfs_read_stats(uint64_t *survivors, uint64_t *theta_steps) {
+  if (!survivors || !theta_steps) return QFS_ERR_NULL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned long long v[2] = {0, 0};
+  e = cudaMemcpy(v, reinterpret_cast<char *>(S->ctrl) + 16, 16, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemset(reinterpret_cast<char *>(S->ctrl) + 16, 0, 16);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *survivors = v[0];
+  *theta_steps = v[1];
+  return QFS_OK;
 }
 
 int qfs_read_status(uint32_t *status_out) {

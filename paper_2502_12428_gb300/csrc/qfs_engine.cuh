@@ -227,9 +227,10 @@ __device__ __forceinline__ bool theta_step(const uint8_t *__restrict__ delta, co
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code (thread 0 writes it).
 template <int P, int FORM, bool DEBUG>
 __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
-                               uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg) {
+                               uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg, int &theta_steps) {
   using Pr = Prime<P>;
   const int tid = threadIdx.x;
+  theta_steps = 0;
   // A1: coefficients, validation, tap tables
   int bad = 0;
   if (tid < 35) {
@@ -311,6 +312,7 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   for (int h = 2; h <= max_h; ++h) {
     const bool any = theta_step<P>(delta, sm, g, g2);
     const int nonzero = __syncthreads_or(any ? 1 : 0);
+    theta_steps = h - 1;
     if (DEBUG)
       for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = g2[i];
     if (g2[Pr::witness] != 0) return h;
@@ -340,6 +342,7 @@ struct FusedParams {
   int sw_len;                         // SW entries to build (max D in this launch + 2)
   unsigned long long *counter;        // work queue head (zeroed before launch)
   uint32_t *status;
+  unsigned long long *stats;          // [0] quartics past the height-1 test, [1] theta steps run
   uint32_t *ws;                       // 2 buffers of ws_words per CTA
   size_t ws_words;
 };
@@ -368,15 +371,21 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
     const FusedGroup &G = prm.g[gi];
     const int64_t row = item - G.item_begin;
     const uint8_t *f = G.coeffs + 35 * row;
-    int h;
+    int h, steps;
     switch (G.p) {
-      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg); break;
-      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg); break;
-      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg); break;
-      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg); break;
-      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg); break;
+      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
+      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
+      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
+      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
+      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
     }
-    if (threadIdx.x == 0) G.heights[row] = (int8_t)h;
+    if (threadIdx.x == 0) {
+      G.heights[row] = (int8_t)h;
+      if (h != 1 && h != -1) {
+        atomicAdd(prm.stats, 1ull);
+        atomicAdd(prm.stats + 1, (unsigned long long)steps);
+      }
+    }
   }
 }
 

@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int m
   uint8_t *gn = gs + Prime<P>::ld;
   build_sw(sm.SW, Prime<P>::D + 2);
   __syncthreads();
-  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, bufA, bufB, status, dbg);
+  int steps = 0;
+  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, bufA, bufB, status, dbg, steps);
   if (threadIdx.x == 0) *h_out = (int8_t)h;
 }
 

@@ -56,12 +56,13 @@ def _lib():
         L.qfs_plan_prepare.argtypes = [c_int, i64]
         L.qfs_shutdown.argtypes = []
         L.qfs_read_status.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+        L.qfs_read_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
         L.qfs_strerror.argtypes = [c_int]
         L.qfs_strerror.restype = ctypes.c_char_p
         L.qfs_last_cuda_error.argtypes = []
         L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
-                     "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_last_cuda_error",
+                     "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages"):
             getattr(L, name).restype = c_int
         _LIB = L
@@ -162,6 +163,13 @@ def read_status():
     v = ctypes.c_uint32(0)
     _check(_lib().qfs_read_status(ctypes.byref(v)), "qfs_read_status")
     return v.value
+
+
+def read_stats():
+    """(survivors, theta_steps) counted by the device since the last call (synchronises)."""
+    a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_lib().qfs_read_stats(ctypes.byref(a), ctypes.byref(b)), "qfs_read_stats")
+    return a.value, b.value
 
 
 def debug_stages(p, coeffs, max_h=10, form="dp4a"):
