@@ -124,6 +124,21 @@ const char *qfs_strerror(int status);
 /* The cudaError_t of the last failed CUDA call inside the library (0 if none). */
 int qfs_last_cuda_error(void);
 
+/* qfs_heights without any allocation, for callers that cannot allocate device memory when they call: code
+   running inside a stream capture in global mode (cudaMalloc there invalidates the capture), code whose device
+   memory is owned by another allocator, and code that must not stall the device (cudaFree synchronises it).
+   The paper has no counterpart; this is a deployment aid.
+   Same arguments, codes and stream semantics as qfs_heights (dp4a form).  All scratch lives in one fixed 64 MiB
+   array of device memory that the library declares statically: every GPU that loads libqfs holds it until the
+   process exits.  The first call on a device looks up that array's device address (cudaGetSymbolAddress), so
+   make the first call on each device before any stream capture.  The array keeps the previous call's contents;
+   each call clears the part that must start at zero.  Calls whose kernels overlap on the GPU (for example calls
+   on two different streams of one device) share the array and race: keep them ordered on one stream.
+   Returns QFS_ERR_NO_MEMORY when one persistent CTA's workspace does not fit in 64 MiB (p = 13); otherwise it
+   runs as many CTAs as fit (p = 7: 39, p = 11: 2), so large p runs slower here than through qfs_heights. */
+int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int max_h, int8_t *heights_out,
+                        cudaStream_t stream);
+
 /* Kernel-level parity hook (tests only need it; it runs the same device code as qfs_heights on ONE quartic).
    coeffs: device, 35 uint8.  All outputs are device int32 arrays in descending-lex order; any may be NULL.
      g_out     C(4p-1,3) values: f^(p-1) mod p

@@ -61,9 +61,10 @@ def _lib():
         L.qfs_strerror.restype = ctypes.c_char_p
         L.qfs_last_cuda_error.argtypes = []
         L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
+        L.qfs_heights_noalloc.argtypes = [c_int, i64, vp, c_int, vp, vp]
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
-                     "qfs_debug_stages"):
+                     "qfs_debug_stages", "qfs_heights_noalloc"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -145,6 +146,23 @@ def heights_multi(groups, max_h=10, stream=None, form=None, engine=None, ctas_pe
     rc = _lib().qfs_heights_multi_ex(len(groups), arr, int(max_h), ctypes.byref(opts), _stream(stream))
     _check(rc, "qfs_heights_multi_ex")
     return outs
+
+
+def heights_noalloc(p, coeffs, max_h=10, out=None, stream=None):
+    """qfs_heights_noalloc: the same heights, computed in the library's fixed 64 MiB device scratch array, with no
+    device allocation inside the call (for callers that cannot allocate then, e.g. during a global-mode stream
+    capture or under another allocator that owns the device).  Make the first call on a device before any capture.
+    Calls that overlap on the GPU share the scratch and race."""
+    _need_cuda(coeffs, torch.uint8, "coeffs")
+    if coeffs.dim() != 2 or coeffs.shape[1] != 35:
+        raise ValueError("coeffs must have shape (n, 35)")
+    if out is None:
+        out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=coeffs.device)
+    _need_cuda(out, torch.int8, "out")
+    rc = _lib().qfs_heights_noalloc(int(p), int(coeffs.shape[0]), coeffs.data_ptr(), int(max_h), out.data_ptr(),
+                                    _stream(stream))
+    _check(rc, "qfs_heights_noalloc")
+    return out
 
 
 def set_default_form(form):
