@@ -22,6 +22,7 @@
 namespace qfs {
 
 constexpr int kThreads = 256;
+constexpr int kMaxUparDecl = 8;
 
 // Status bits (atomicOr into the device status word).
 constexpr uint32_t kStatusInexactDivision = 1u;
@@ -40,21 +41,77 @@ struct Smem {
   uint32_t tapword[15];   // dp4a tap words per (uI, sI) pair: byte k = a(uI, sI, 3-k)
   uint32_t pair_mask;     // bit tri(uI)+sI set iff that pair has a nonzero tap
   int powp[kMaxP];        // c^p mod p^2
+  int slot_tab[2][kMaxUparDecl + 4];  // ring word offsets of the slices a chain round reads (double buffered)
   int64_t item;
   int flag;
   // followed in dynamic shared memory by two byte arrays of ld entries: g (current iterate) and g_next
 };
 
-__host__ __device__ constexpr size_t smem_bytes_for(int p) {
-  return sizeof(Smem) + 2 * (size_t)tet(4 * (p - 1) + 1) + 16;
+// Dynamic shared memory layout: [Smem][g: ld][g_next: ld][pad to 16 B][chain ring].
+__host__ __device__ constexpr size_t ring_offset_for(int max_ld) {
+  return (sizeof(Smem) + 2 * (size_t)max_ld + 15) & ~(size_t)15;
 }
 
 // ------------------------------------------------------------------------------------------------ chain step
-// out := in * f (mod p^2), in of degree m_in, out of degree m_in + 4.  When LAST, the Delta_1 epilogue turns
-// G into Delta and writes residues mod p.
-template <int P, int FORM, bool LAST, bool DEBUG>
-__device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
-                                           const Smem &sm, const uint8_t *gs, uint32_t *status, DebugPtrs dbg);
+// out := in * f (mod p^2), in of degree m_in, out of degree m_in + 4 (one product of the chain).  When LAST, the
+// Delta_1 epilogue turns G into Delta and writes residues mod p.
+//
+// Tiling.  Output columns are taken in blocks of 32 (s0 .. s0+31) and each block sweeps the slices u = s0 .. m_out,
+// UPAR slices per round.  Output slice u reads input slices u-4 .. u (uI = 4 - i1) and columns s-4 .. s, so a ring
+// of shared-memory slots holds input slices restricted to columns s0-4 .. s0+31, zero-filled outside the input
+// cone: the inner loop has no bounds checks.  The next UPAR slices stream in with 16-byte cp.async while the
+// current ones are computed.  Work items are flat: one lane = one (column, 16-byte chunk) pair of the round, so
+// columns that do not exist yet in a slice (s > u) cost nothing.  A slot column holds chunk 0 = zeros (input words
+// -4..-1) followed by the column's chunks, so output chunk c reads slot chunks c and c+1 (input words 4c-4..4c+3).
+// Outputs past a column's end come out as zero by themselves (their inputs are all padding), so no output needs a
+// bounds check outside the Delta_1 epilogue.
+constexpr int kRingBudgetSmallP = 16384;   // ring words for p <= 7 (64 KB)
+constexpr int kRingBudgetLargeP = 26624;   // ring words for p >= 11 (104 KB)
+constexpr int kMaxUpar = 8;
+
+struct ChainTile {
+  int CR, stride, slot_words, upar, nslot;
+};
+
+__host__ __device__ inline ChainTile chain_tile(int s0, int m_out, int budget_words) {
+  ChainTile T;
+  const int s_hi = min(s0 + 31, m_out);
+  T.CR = chunks_of(s_hi);
+  T.stride = 4 * (T.CR + 1);
+  T.slot_words = 36 * T.stride;
+  const int per_slice = chunk_prefix(s_hi + 1) - chunk_prefix(s0);
+  int up = (512 + per_slice - 1) / per_slice;
+  up = max(1, min(kMaxUpar, up));
+  while (up > 1 && (2 * up + 4) * T.slot_words > budget_words) --up;
+  T.upar = up;
+  T.nslot = 2 * up + 4;
+  return T;
+}
+
+__host__ __device__ inline int ring_budget(int p) { return p <= 7 ? kRingBudgetSmallP : kRingBudgetLargeP; }
+
+// Shared-memory words the ring needs over every product of the chain for prime p.
+__host__ __device__ inline int chain_slot_words(int p) {
+  const int D = 4 * p * (p - 1);
+  int best = 0;
+  for (int m_out = 8; m_out <= D; m_out += 4)
+    for (int s0 = 0; s0 <= m_out; s0 += 32) {
+      const ChainTile T = chain_tile(s0, m_out, ring_budget(p));
+      best = max(best, T.nslot * T.slot_words);
+    }
+  return best;
+}
+
+__host__ __device__ inline size_t smem_bytes_for(int p) {
+  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)chain_slot_words(p);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t *smem, const uint32_t *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 namespace detail {
 
@@ -64,66 +121,62 @@ struct Pair {
   static constexpr int tap0 = tet(UI) + tri(SI);  // tap index of tI = 0
 };
 
-// Loads the two input words that cover t' in [4w-4, 4w+3] of input column (u-UI, s-SI); false if the column is
-// outside the degree-m_in cone.
-template <int UI, int SI>
-__device__ __forceinline__ bool load_pair(const uint32_t *__restrict__ in, const int *SW, int m_in, int u, int s,
-                                          int w, uint32_t &lo, uint32_t &hi) {
-  const int u2 = u - UI, s2 = s - SI;
-  if (s2 < 0 || s2 > u2 || u2 > m_in) return false;
-  const int base = SW[u2] + colw(s2);
-  const int nw = (s2 >> 2) + 1;
-  hi = (w < nw) ? __ldg(in + base + w) : 0u;
-  lo = (w >= 1) ? __ldg(in + base + w - 1) : 0u;
-  return true;
-}
-
-template <int UI, int SI>
-__device__ __forceinline__ void pair_int32(const uint32_t *__restrict__ in, const int *SW, int m_in, int u, int s,
-                                           int w, const int *taps, uint32_t mask, int (&acc)[4]) {
-  constexpr int PI = Pair<UI, SI>::index;
-  if (!((mask >> PI) & 1u)) return;
-  uint32_t lo, hi;
-  if (!load_pair<UI, SI>(in, SW, m_in, u, s, w, lo, hi)) return;
-  int v[8];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    v[j] = (int)((lo >> (8 * j)) & 0xFFu);
-    v[4 + j] = (int)((hi >> (8 * j)) & 0xFFu);
+// Contribution of pair (UI, SI) to the four output words (16 outputs) of one item.  `col` points at slot chunk c
+// of input column s - SI; x[j] = input word 4c - 4 + j.
+template <int UI, int SI, int FORM>
+__device__ __forceinline__ void pair_item(const uint32_t *col, const Smem &sm, int (&acc)[4][4]) {
+  uint32_t x[8];
+  {
+    const uint4 a = *reinterpret_cast<const uint4 *>(col);
+    const uint4 b = *reinterpret_cast<const uint4 *>(col + 4);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
   }
+  if (FORM == 0) {
+    int v[20];
 #pragma unroll
-  for (int tI = 0; tI <= SI; ++tI) {
-    const int a = taps[Pair<UI, SI>::tap0 + tI];
+    for (int j = 0; j < 20; ++j) v[j] = (int)((x[3 + (j >> 2)] >> (8 * (j & 3))) & 0xFFu);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r] += a * v[4 + r - tI];
-  }
-}
-
-template <int UI, int SI>
-__device__ __forceinline__ void pair_dp4a(const uint32_t *__restrict__ in, const int *SW, int m_in, int u, int s,
-                                          int w, const Smem &sm, uint32_t mask, int (&acc)[4]) {
-  constexpr int PI = Pair<UI, SI>::index;
-  if (!((mask >> PI) & 1u)) return;
-  uint32_t lo, hi;
-  if (!load_pair<UI, SI>(in, SW, m_in, u, s, w, lo, hi)) return;
-  if (SI == 0) {
-    // single tap at t' = t: byte r of hi
-    const uint32_t a = (uint32_t)sm.taps[Pair<UI, SI>::tap0];
+    for (int tI = 0; tI <= SI; ++tI) {
+      const int a = sm.taps[Pair<UI, SI>::tap0 + tI];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r] = (int)__dp4a(hi, a << (8 * r), (unsigned)acc[r]);
-  } else {
-    const uint32_t tw = sm.tapword[PI];
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      // window byte k = in(t - 3 + k) for t = 4w + r: bytes r+1 .. r+4 of the 8-byte (lo, hi) concatenation
-      const uint32_t win = __byte_perm(lo, hi, (unsigned)((r + 1) | ((r + 2) << 4) | ((r + 3) << 8) | ((r + 4) << 12)));
-      acc[r] = (int)__dp4a(win, tw, (unsigned)acc[r]);
+        for (int r = 0; r < 4; ++r) acc[q][r] += a * v[4 + 4 * q + r - tI];
     }
-    if (SI == 4) {
-      // the tap at tI = 4 reads in(t - 4) = byte r of lo
-      const uint32_t a4 = (uint32_t)sm.taps[Pair<UI, SI>::tap0 + 4];
+  } else {
+    if (SI == 0) {
+      const uint32_t a = (uint32_t)sm.taps[Pair<UI, SI>::tap0];
+      const uint32_t a0 = a, a1 = a << 8, a2 = a << 16, a3 = a << 24;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[r] = (int)__dp4a(lo, a4 << (8 * r), (unsigned)acc[r]);
+      for (int q = 0; q < 4; ++q) {
+        acc[q][0] = (int)__dp4a(x[4 + q], a0, (unsigned)acc[q][0]);
+        acc[q][1] = (int)__dp4a(x[4 + q], a1, (unsigned)acc[q][1]);
+        acc[q][2] = (int)__dp4a(x[4 + q], a2, (unsigned)acc[q][2]);
+        acc[q][3] = (int)__dp4a(x[4 + q], a3, (unsigned)acc[q][3]);
+      }
+    } else {
+      const uint32_t tw = sm.tapword[Pair<UI, SI>::index];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // window byte k = in(t - 3 + k), t = 4w + r: bytes r+1 .. r+4 of (lo = word w-1, hi = word w)
+        acc[q][0] = (int)__dp4a(__byte_perm(x[3 + q], x[4 + q], 0x4321u), tw, (unsigned)acc[q][0]);
+        acc[q][1] = (int)__dp4a(__byte_perm(x[3 + q], x[4 + q], 0x5432u), tw, (unsigned)acc[q][1]);
+        acc[q][2] = (int)__dp4a(__byte_perm(x[3 + q], x[4 + q], 0x6543u), tw, (unsigned)acc[q][2]);
+        acc[q][3] = (int)__dp4a(x[4 + q], tw, (unsigned)acc[q][3]);
+      }
+      if (SI == 4) {
+        // the tap at tI = 4 reads in(t - 4) = byte r of word w - 1
+        const uint32_t a = (uint32_t)sm.taps[Pair<UI, SI>::tap0 + 4];
+        const uint32_t a0 = a, a1 = a << 8, a2 = a << 16, a3 = a << 24;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q][0] = (int)__dp4a(x[3 + q], a0, (unsigned)acc[q][0]);
+          acc[q][1] = (int)__dp4a(x[3 + q], a1, (unsigned)acc[q][1]);
+          acc[q][2] = (int)__dp4a(x[3 + q], a2, (unsigned)acc[q][2]);
+          acc[q][3] = (int)__dp4a(x[3 + q], a3, (unsigned)acc[q][3]);
+        }
+      }
     }
   }
 }
@@ -131,58 +184,131 @@ __device__ __forceinline__ void pair_dp4a(const uint32_t *__restrict__ in, const
 #define QFS_FOR_EACH_PAIR(X) \
   X(0, 0) X(1, 0) X(1, 1) X(2, 0) X(2, 1) X(2, 2) X(3, 0) X(3, 1) X(3, 2) X(3, 3) X(4, 0) X(4, 1) X(4, 2) X(4, 3) X(4, 4)
 
+// All 15 pairs of one item; DENSE skips the per-pair test of the nonzero-pair mask.
+template <int FORM, bool DENSE>
+__device__ __forceinline__ void item_pairs(const uint32_t *sb0, const uint32_t *sb1, const uint32_t *sb2,
+                                           const uint32_t *sb3, const uint32_t *sb4, int stride, uint32_t mask,
+                                           const Smem &sm, int (&acc)[4][4]) {
+#define QFS_PAIR(UI, SI)                                                                                      \
+  if (DENSE || ((mask >> Pair<UI, SI>::index) & 1u)) pair_item<UI, SI, FORM>(sb##UI - SI * stride, sm, acc);
+  QFS_FOR_EACH_PAIR(QFS_PAIR)
+#undef QFS_PAIR
+}
+
 }  // namespace detail
 
 template <int P, int FORM, bool LAST, bool DEBUG>
 __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
-                                           const Smem &sm, const uint8_t *gs, uint32_t *status, DebugPtrs dbg) {
+                                           Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
+                                           DebugPtrs dbg) {
   using Pr = Prime<P>;
   const int m_out = m_in + 4;
-  const int total = sm.SW[m_out + 1];
   const uint32_t mask = sm.pair_mask;
-  int taps[35];
-  if (FORM == 0) {
-#pragma unroll
-    for (int i = 0; i < 35; ++i) taps[i] = sm.taps[i];
-  }
+  const bool dense = mask == 0x7FFFu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int nthreads = blockDim.x;
   bool bad = false;
-  for (int k = threadIdx.x; k < total; k += blockDim.x) {
-    int u, s, w;
-    decode_word(k, m_out, sm.SW, u, s, w);
-    int acc[4] = {0, 0, 0, 0};
-    if (FORM == 0) {
-#define QFS_PAIR_INT32(UI, SI) detail::pair_int32<UI, SI>(in, sm.SW, m_in, u, s, w, taps, mask, acc);
-      QFS_FOR_EACH_PAIR(QFS_PAIR_INT32)
-#undef QFS_PAIR_INT32
-    } else {
-#define QFS_PAIR_DP4A(UI, SI) detail::pair_dp4a<UI, SI>(in, sm.SW, m_in, u, s, w, sm, mask, acc);
-      QFS_FOR_EACH_PAIR(QFS_PAIR_DP4A)
-#undef QFS_PAIR_DP4A
-    }
-    uint32_t word = 0, gword = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int t = 4 * w + r;
-      int G = acc[r] % Pr::p2;  // acc >= 0
-      uint32_t byte = 0;
-      if (t <= s) {
-        if (LAST) {
-          if (DEBUG) gword |= (uint32_t)G << (8 * r);
-          if ((u % P) == 0 && (s % P) == 0 && (t % P) == 0) {
-            const int J = tet(u / P) + tri(s / P) + t / P;
-            G = G - sm.powp[gs[J]];
-            if (G < 0) G += Pr::p2;
-          }
-          if (G % P) bad = true;
-          byte = (uint32_t)(G / P);
-        } else {
-          byte = (uint32_t)G;
-        }
+  for (int s0 = 0; s0 <= m_out; s0 += 32) {
+    const ChainTile T = chain_tile(s0, m_out, ring_budget(P));
+    const int s_last = min(s0 + 31, m_out);
+    const int F0 = chunk_prefix(s0);
+    const int ccols = T.CR + 1;  // slot chunks per column
+    // fetch input slice u2 (columns s0-4 .. s0+31) into ring slot `slot`, zeros outside the input cone
+    auto fetch = [&](int u2, int slot) {
+      uint32_t *dst = ring + slot * T.slot_words;
+      const bool slice_ok = u2 >= 0 && u2 <= m_in;
+      const int base_u = slice_ok ? sm.SW[u2] : 0;
+      for (int i = threadIdx.x; i < 36 * ccols; i += nthreads) {
+        const int cs = i / ccols, j = i - cs * ccols;
+        const int s2 = s0 - 4 + cs;
+        const bool ok = slice_ok && j >= 1 && s2 >= 0 && s2 <= u2 && j - 1 < chunks_of(s2);
+        const uint32_t *src = ok ? in + base_u + colw(s2) + 4 * (j - 1) : in;
+        cp_async16(dst + cs * T.stride + 4 * j, src, ok);
       }
-      word |= byte << (8 * r);
+    };
+    for (int u2 = s0 - 4; u2 < s0 + T.upar; ++u2) fetch(u2, (u2 - s0 + 4) % T.nslot);
+    cp_async_commit();
+    if (threadIdx.x < kMaxUpar + 4) {
+      const int u2 = s0 - 4 + (int)threadIdx.x;
+      sm.slot_tab[0][threadIdx.x] = ((u2 - s0 + 4) % T.nslot) * T.slot_words;
     }
-    out[k] = word;
-    if (DEBUG && LAST) dbg.G[k] = gword;
+    cp_async_wait_all();
+    __syncthreads();
+    int tab = 0;
+    for (int u = s0; u <= m_out; u += T.upar) {
+      for (int u2 = u + T.upar; u2 < u + 2 * T.upar && u2 <= m_out; ++u2) fetch(u2, (u2 - s0 + 4) % T.nslot);
+      cp_async_commit();
+      if (threadIdx.x < kMaxUpar + 4) {  // slot table of the next round (slices u + upar - 4 ..)
+        const int u2 = u + T.upar - 4 + (int)threadIdx.x;
+        sm.slot_tab[tab ^ 1][threadIdx.x] = ((u2 - s0 + 4) % T.nslot) * T.slot_words;
+      }
+      const int nU = min(T.upar, m_out - u + 1);
+      // chunk prefix over the round's slices: slice u+du holds columns s0 .. min(s_last, u+du)
+      int pre[kMaxUpar + 1];
+      pre[0] = 0;
+#pragma unroll
+      for (int du = 0; du < kMaxUpar; ++du) {
+        const int cols_hi = min(s_last, u + du);
+        pre[du + 1] = pre[du] + (du < nU ? chunk_prefix(cols_hi + 1) - F0 : 0);
+      }
+      const int total = pre[kMaxUpar];
+      const int *stab = sm.slot_tab[tab];
+      for (int it = warp; it * 32 < total; it += nwarps) {
+        const int g = it * 32 + lane;
+        if (g >= total) continue;
+        int du = 0, gbase = 0;
+#pragma unroll
+        for (int j = 1; j < kMaxUpar; ++j)
+          if (g >= pre[j]) { du = j; gbase = pre[j]; }
+        const int uo = u + du;
+        int s, c;
+        decode_chunk(g - gbase + F0, s, c);
+        int acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+        const int colbase = (s - s0 + 4) * T.stride + 4 * c;
+        const uint32_t *sb0 = ring + stab[du + 4] + colbase;
+        const uint32_t *sb1 = ring + stab[du + 3] + colbase;
+        const uint32_t *sb2 = ring + stab[du + 2] + colbase;
+        const uint32_t *sb3 = ring + stab[du + 1] + colbase;
+        const uint32_t *sb4 = ring + stab[du + 0] + colbase;
+        if (dense)
+          detail::item_pairs<FORM, true>(sb0, sb1, sb2, sb3, sb4, T.stride, mask, sm, acc);
+        else
+          detail::item_pairs<FORM, false>(sb0, sb1, sb2, sb3, sb4, T.stride, mask, sm, acc);
+        uint32_t word[4], gword[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          word[q] = 0;
+          gword[q] = 0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            int G = acc[q][r] % Pr::p2;  // acc >= 0; zero past the column's end
+            if (LAST) {
+              const int t = 16 * c + 4 * q + r;
+              if (DEBUG) gword[q] |= (uint32_t)G << (8 * r);
+              if (t <= s && (uo % P) == 0 && (s % P) == 0 && (t % P) == 0) {
+                const int J = tet(uo / P) + tri(s / P) + t / P;
+                G = G - sm.powp[gs[J]];
+                if (G < 0) G += Pr::p2;
+              }
+              if (G % P) bad = true;
+              G /= P;
+            }
+            word[q] |= (uint32_t)G << (8 * r);
+          }
+        }
+        const int o = sm.SW[uo] + colw(s) + 4 * c;
+        *reinterpret_cast<uint4 *>(out + o) = make_uint4(word[0], word[1], word[2], word[3]);
+        if (DEBUG && LAST) *reinterpret_cast<uint4 *>(dbg.G + o) = make_uint4(gword[0], gword[1], gword[2], gword[3]);
+      }
+      tab ^= 1;
+      cp_async_wait_all();
+      __syncthreads();
+    }
   }
   if (bad) atomicOr(status, kStatusInexactDivision);
 }
@@ -213,7 +339,7 @@ __device__ __forceinline__ bool theta_step(const uint8_t *__restrict__ delta, co
         if (tlo > thi) continue;
         const uint8_t *dcol = delta + 4 * (sm.SW[eu] + colw(es)) + et0;  // Delta(eu, es, et0 - tc) = dcol[-tc]
         const uint8_t *gcol = g + tet(uc) + tri(sc);
-        for (int tc = tlo; tc <= thi; ++tc) acc += (int)__ldg(dcol - tc) * (int)gcol[tc];
+        for (int tc = tlo; tc <= thi; ++tc) acc += (int)dcol[-tc] * (int)gcol[tc];
       }
     }
     const int v = acc % P;
@@ -227,7 +353,8 @@ __device__ __forceinline__ bool theta_step(const uint8_t *__restrict__ delta, co
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code (thread 0 writes it).
 template <int P, int FORM, bool DEBUG>
 __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
-                               uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg, int &theta_steps) {
+                               uint32_t *ring, uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg,
+                               int &theta_steps) {
   using Pr = Prime<P>;
   const int tid = threadIdx.x;
   theta_steps = 0;
@@ -260,35 +387,33 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
       sm.powp[c] = v;
     }
   }
-  // f into bufA (padded, degree 4)
-  for (int k = tid; k < sm.SW[5]; k += blockDim.x) {
-    int u, s, w;
-    decode_word(k, 4, sm.SW, u, s, w);
-    uint32_t word = 0;
-    for (int r = 0; r < 4; ++r) {
-      const int t = 4 * w + r;
-      if (t <= s) word |= (uint32_t)sm.taps[tet(u) + tri(s) + t] << (8 * r);
-    }
-    bufA[k] = word;
+  // f into bufA (padded, degree 4: every column is one chunk)
+  for (int k = tid; k < sm.SW[5] / 4; k += blockDim.x) {
+    int u, s, c;
+    decode_form_chunk(k, 4, sm.SW, u, s, c);
+    uint32_t words[4] = {0, 0, 0, 0};
+    for (int t = 0; t <= s; ++t) words[t >> 2] |= (uint32_t)sm.taps[tet(u) + tri(s) + t] << (8 * (t & 3));
+    *reinterpret_cast<uint4 *>(bufA + 4 * k) = make_uint4(words[0], words[1], words[2], words[3]);
   }
   __syncthreads();
   // A2: f~^(k+1) = f~^k * f~ for k = 1 .. p-2
   uint32_t *cur = bufA, *nxt = bufB;
   int m = 4;
   for (int k = 1; k <= P - 2; ++k) {
-    chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, gs, status, dbg);
+    chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
     __syncthreads();
     uint32_t *t = cur; cur = nxt; nxt = t;
     m += 4;
   }
   // A3: g = f^(p-1) mod p into shared memory (packed); witness test
-  for (int k = tid; k < sm.SW[Pr::d + 1]; k += blockDim.x) {
-    int u, s, w;
-    decode_word(k, Pr::d, sm.SW, u, s, w);
-    const uint32_t word = cur[k];
-    for (int r = 0; r < 4; ++r) {
-      const int t = 4 * w + r;
-      if (t <= s) gs[tet(u) + tri(s) + t] = (uint8_t)(((word >> (8 * r)) & 0xFFu) % P);
+  for (int k = tid; k < sm.SW[Pr::d + 1] / 4; k += blockDim.x) {
+    int u, s, c;
+    decode_form_chunk(k, Pr::d, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(cur + 4 * k);
+    const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16; ++b) {
+      const int t = 16 * c + b;
+      if (t <= s) gs[tet(u) + tri(s) + t] = (uint8_t)(((words[b >> 2] >> (8 * (b & 3))) & 0xFFu) % P);
     }
   }
   __syncthreads();
@@ -297,12 +422,12 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   if (gs[Pr::witness] != 0) return 1;
   // A4 + A5: chain to f~^(p(p-1)); the last product carries the Delta_1 epilogue
   for (int k = P - 1; k <= P * (P - 1) - 2; ++k) {
-    chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, gs, status, dbg);
+    chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
     __syncthreads();
     uint32_t *t = cur; cur = nxt; nxt = t;
     m += 4;
   }
-  chain_step<P, FORM, true, DEBUG>(cur, nxt, m, sm, gs, status, dbg);
+  chain_step<P, FORM, true, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
   __syncthreads();
   if (DEBUG)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = nxt[k];
@@ -356,6 +481,7 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
   int max_ld = 0;
   for (int i = 0; i < prm.n_groups; ++i) max_ld = max(max_ld, tet(4 * (prm.g[i].p - 1) + 1));
   uint8_t *gn = gs + max_ld;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(max_ld));
   build_sw(sm.SW, prm.sw_len);
   uint32_t *bufA = prm.ws + (size_t)blockIdx.x * 2 * prm.ws_words;
   uint32_t *bufB = bufA + prm.ws_words;
@@ -373,11 +499,11 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
     const uint8_t *f = G.coeffs + 35 * row;
     int h, steps;
     switch (G.p) {
-      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
-      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
-      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
-      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
-      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, bufA, bufB, prm.status, dbg, steps); break;
+      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
+      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
+      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
+      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
+      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
     }
     if (threadIdx.x == 0) {
       G.heights[row] = (int8_t)h;

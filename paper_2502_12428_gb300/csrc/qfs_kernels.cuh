@@ -19,10 +19,11 @@ __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int m
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   uint8_t *gs = smem_raw + sizeof(Smem);
   uint8_t *gn = gs + Prime<P>::ld;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(Prime<P>::ld));
   build_sw(sm.SW, Prime<P>::D + 2);
   __syncthreads();
   int steps = 0;
-  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, bufA, bufB, status, dbg, steps);
+  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, ring, bufA, bufB, status, dbg, steps);
   if (threadIdx.x == 0) *h_out = (int8_t)h;
 }
 
@@ -34,6 +35,10 @@ struct FormLauncher {
   static cudaError_t debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA, uint32_t *bufB,
                            uint32_t *status, DebugPtrs dbg, cudaStream_t st);
 };
+
+#define QFS_DEBUG_LAUNCH(PP, FORM)                                                                            \
+  e = cudaFuncSetAttribute(debug_kernel<PP, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+  if (e == cudaSuccess) debug_kernel<PP, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg)
 
 #define QFS_DEFINE_FORM_LAUNCHER(FORM)                                                                        \
   template <>                                                                                                 \
@@ -55,13 +60,15 @@ struct FormLauncher {
   cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st) {   \
     const size_t smem = smem_bytes_for(p);                                                                    \
+    cudaError_t e = cudaSuccess;                                                                              \
     switch (p) {                                                                                              \
-      case 3: debug_kernel<3, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
-      case 5: debug_kernel<5, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
-      case 7: debug_kernel<7, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
-      case 11: debug_kernel<11, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
-      default: debug_kernel<13, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg); break; \
+      case 3: QFS_DEBUG_LAUNCH(3, FORM); break;                                                               \
+      case 5: QFS_DEBUG_LAUNCH(5, FORM); break;                                                               \
+      case 7: QFS_DEBUG_LAUNCH(7, FORM); break;                                                               \
+      case 11: QFS_DEBUG_LAUNCH(11, FORM); break;                                                             \
+      default: QFS_DEBUG_LAUNCH(13, FORM); break;                                                             \
     }                                                                                                         \
+    if (e != cudaSuccess) return e;                                                                           \
     return cudaGetLastError();                                                                                \
   }
 

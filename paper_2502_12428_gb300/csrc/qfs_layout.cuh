@@ -9,10 +9,11 @@
 // prints quartics (Figures 4-7) and the order of every array that crosses the C ABI.  A form of degree m has
 // C(m+3,3) = tet(m+1) entries (the paper's l_d, Sec. 4).
 //
-// Padded layout (device workspaces): the same order, but every column (u, s) -- the s+1 entries t = 0..s -- starts
-// on a 4-byte boundary and occupies W(s) = s/4 + 1 words of four one-byte residues; padding bytes are zero.
-// Word offset of column (u, s) = SW[u] + colw(s), where colw(s) = sum_{s' < s} W(s') = (q+1)(2q+r) for s = 4q+r
-// and SW[u] = sum_{v < u} colw(v+1).  SW does not depend on m; a degree-m form uses words [0, SW[m+1]).
+// Padded layout (device workspaces): the same order, but every column (u, s) -- the s+1 entries t = 0..s, one byte
+// each -- starts on a 16-byte boundary and occupies chunks(s) = s/16 + 1 chunks of four 32-bit words; padding bytes
+// are zero.  Word offset of column (u, s) = SW[u] + 4 F(s), where F(s) = sum_{s' < s} chunks(s') = (q+1)(8q+r) for
+// s = 16q + r, and SW[u] = sum_{v < u} 4 F(v+1).  SW does not depend on m; a degree-m form uses words
+// [0, SW[m+1]).
 #pragma once
 #include <cstdint>
 
@@ -20,7 +21,10 @@ namespace qfs {
 
 __host__ __device__ constexpr int tet(int u) { return u * (u + 1) * (u + 2) / 6; }
 __host__ __device__ constexpr int tri(int s) { return s * (s + 1) / 2; }
-__host__ __device__ constexpr int colw(int s) { return ((s >> 2) + 1) * (2 * (s >> 2) + (s & 3)); }
+__host__ __device__ constexpr int chunks_of(int s) { return (s >> 4) + 1; }
+__host__ __device__ constexpr int chunk_prefix(int s) { return ((s >> 4) + 1) * (8 * (s >> 4) + (s & 15)); }
+// word offset of column s inside its slice (16-byte aligned)
+__host__ __device__ constexpr int colw(int s) { return 4 * chunk_prefix(s); }
 __host__ __device__ constexpr int n_monomials(int m) { return tet(m + 1); }
 
 // Largest prime the engine accepts and the derived sizes.
@@ -61,22 +65,28 @@ __device__ __forceinline__ void build_sw(int *SW, int n) {
   }
 }
 
-// Flat word index k of a degree-m padded form -> (u, s, w): column (u, s), word w (entries t = 4w .. 4w+3).
-__device__ __forceinline__ void decode_word(int k, int m, const int *SW, int &u, int &s, int &w) {
+// Flat chunk index h of one slice (h = F(s) + c) -> column s and chunk c.
+__device__ __forceinline__ void decode_chunk(int h, int &s, int &c) {
+  int q = (int)((sqrtf(1.0f + 0.5f * (float)h) - 1.0f) * 0.5f);
+  while (8 * (q + 1) * (q + 2) <= h) ++q;
+  while (q > 0 && 8 * q * (q + 1) > h) --q;
+  const int rem = h - 8 * q * (q + 1);
+  int rr = (int)((float)rem / (float)(q + 1));
+  while (rr * (q + 1) > rem) --rr;
+  while ((rr + 1) * (q + 1) <= rem) ++rr;
+  c = rem - rr * (q + 1);
+  s = 16 * q + rr;
+}
+
+// Flat chunk index k of a whole degree-m padded form -> (u, s, c); SW is the slice table (in words).
+__device__ __forceinline__ void decode_form_chunk(int k, int m, const int *SW, int &u, int &s, int &c) {
   int lo = 0, hi = m;
   while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (SW[mid] <= k) lo = mid; else hi = mid - 1;
+    const int mid = (lo + hi + 1) >> 1;
+    if (SW[mid] <= 4 * k) lo = mid; else hi = mid - 1;
   }
   u = lo;
-  int kk = k - SW[u];
-  int q = (int)((sqrtf(2.0f * (float)kk + 1.0f) - 1.0f) * 0.5f);
-  while (2 * (q + 1) * (q + 2) <= kk) ++q;
-  while (q > 0 && 2 * q * (q + 1) > kk) --q;
-  int rem = kk - 2 * q * (q + 1);
-  int r = rem / (q + 1);
-  w = rem - r * (q + 1);
-  s = 4 * q + r;
+  decode_chunk(k - (SW[u] >> 2), s, c);
 }
 
 // Packed index i of a form (degree <= kMaxD) -> (u, s, t).
