@@ -102,8 +102,11 @@ __host__ __device__ inline int chain_slot_words(int p) {
   return best;
 }
 
+__host__ __device__ inline int theta_ring_words_for(int p);
+
 __host__ __device__ inline size_t smem_bytes_for(int p) {
-  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)chain_slot_words(p);
+  const int w = max(chain_slot_words(p), theta_ring_words_for(p));
+  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)w;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t *smem, const uint32_t *gmem, bool valid) {
@@ -349,6 +352,153 @@ __device__ __forceinline__ bool theta_step(const uint8_t *__restrict__ delta, co
   return any;
 }
 
+// Theta with Delta streamed through shared memory (p <= 7).  Round e_u loads Delta slice e_u (16-byte cp.async,
+// double buffered) and serves every pair (output slice u_r, g slice u_c) with p u_r + 3(p-1) - u_c = e_u, so each
+// Delta slice is read once per step.  In shared memory every Delta column sits between two 32-byte zero guards and
+// every g column is stored reversed (R[j] = g[s_c - j], zero padded to whole words): the inner product of output
+// (s_r, t_r) with g column (u_c, s_c) is then sum_k dp4a(Delta bytes A+4k .. A+4k+3, R word k) with
+// A = p t_r + (p-1) - s_c, over the whole padded column -- indices outside the column land on zeros.
+// Partial sums accumulate in a shared int32 array, one owner thread per output and round.
+template <int P>
+__host__ __device__ constexpr bool theta_in_smem() { return P <= 7; }
+
+__host__ __device__ constexpr int rcolw(int s) { return ((s >> 2) + 1) * (2 * (s >> 2) + (s & 3)); }
+
+template <int P>
+struct ThetaSmem {
+  static constexpr int d = 4 * (P - 1), D = 4 * P * (P - 1);
+  static constexpr int kGuard = 32;
+  // byte offset of Delta column e_s inside a slot (data after the leading guard)
+  static __host__ __device__ constexpr int col_off(int es) { return 16 * chunk_prefix(es) + kGuard * es + kGuard; }
+  static constexpr int slot_bytes = 16 * chunk_prefix(D + 1) + kGuard * (D + 1) + kGuard;   // + trailing guard
+  static constexpr int slot_words = slot_bytes / 4;
+  static constexpr int rwords = 0;
+};
+
+template <int P>
+__host__ __device__ constexpr int theta_ring_words() {
+  // two Delta slots, the reversed g columns, the int32 accumulators and the reversed-column slice table
+  using T = ThetaSmem<P>;
+  int r = 0;
+  for (int u = 0; u <= T::d; ++u) r += rcolw(u + 1);
+  return 2 * T::slot_words + r + tet(T::d + 1) + (T::d + 2);
+}
+
+template <int P>
+__device__ __forceinline__ bool theta_step_smem(const uint32_t *__restrict__ delta, const Smem &sm,
+                                                const uint8_t *__restrict__ g, uint8_t *__restrict__ gn,
+                                                uint32_t *ring) {
+  using Pr = Prime<P>;
+  using T = ThetaSmem<P>;
+  constexpr int d = Pr::d, D = Pr::D;
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  uint32_t *slots = ring;                                   // 2 x slot_words
+  uint32_t *R = ring + 2 * T::slot_words;                   // reversed g columns
+  int rwords = 0;
+  for (int u = 0; u <= d; ++u) rwords += rcolw(u + 1);
+  int *acc = reinterpret_cast<int *>(R + rwords);           // ld int32
+  int *RSW = acc + Pr::ld;                                  // d+2 slice offsets (words) of R
+  // zero the guards of both slots (fetches never write them), the accumulators; build R
+  for (int i = tid; i < 2 * T::slot_words; i += nthreads) slots[i] = 0;
+  for (int i = tid; i < Pr::ld; i += nthreads) acc[i] = 0;
+  if (tid == 0) {
+    int a = 0;
+    for (int u = 0; u <= d + 1; ++u) { RSW[u] = a; a += rcolw(u + 1); }
+  }
+  __syncthreads();
+  for (int i = tid; i < rwords; i += nthreads) {
+    // word i of R: find its column (u_c, s_c) and word k
+    int u = 0;
+    while (RSW[u + 1] <= i) ++u;
+    int rem = i - RSW[u];
+    int sc = 0;
+    while (rcolw(sc + 1) <= rem) ++sc;
+    const int k = rem - rcolw(sc);
+    const uint8_t *gcol = g + tet(u) + tri(sc);
+    uint32_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * k + b;
+      if (j <= sc) w |= (uint32_t)gcol[sc - j] << (8 * b);
+    }
+    R[i] = w;
+  }
+  auto fetch = [&](int eu, int buf) {
+    uint8_t *dst = reinterpret_cast<uint8_t *>(slots + buf * T::slot_words);
+    const uint32_t *src = delta + sm.SW[eu];
+    // column es: chunks_of(es) chunks at col_off(es); the flat chunk index runs over the slice
+    const int nchunks = chunk_prefix(eu + 1);
+    for (int i = tid; i < nchunks; i += nthreads) {
+      int es, c;
+      decode_chunk(i, es, c);
+      cp_async16(reinterpret_cast<uint32_t *>(dst + T::col_off(es) + 16 * c), src + 4 * i, true);
+    }
+  };
+  __syncthreads();
+  fetch(0, 0);
+  cp_async_commit();
+  for (int eu = 0; eu <= D; ++eu) {
+    if (eu + 1 <= D) fetch(eu + 1, (eu + 1) & 1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::);
+    __syncthreads();
+    const uint8_t *dsl = reinterpret_cast<const uint8_t *>(slots + (eu & 1) * T::slot_words);
+    // output slices served by this round: u_c = p u_r + 3(p-1) - eu in [0, d]
+    const int ur_lo = max(0, (eu - 3 * (P - 1) + P - 1) / P);
+    const int ur_hi = min(d, (eu - 3 * (P - 1) + d) / P);
+    int total = 0;
+    for (int ur = ur_lo; ur <= ur_hi; ++ur) total += tri(ur + 1);
+    for (int item = tid; item < total; item += nthreads) {
+      int ur = ur_lo, f = item;
+      while (f >= tri(ur + 1)) { f -= tri(ur + 1); ++ur; }
+      int sr = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
+      while (tri(sr) > f) --sr;
+      while (tri(sr + 1) <= f) ++sr;
+      const int tr = f - tri(sr);
+      const int uc = P * ur + 3 * (P - 1) - eu;
+      const int E = P * tr + (P - 1);
+      const uint32_t *Rs = R + RSW[uc];
+      unsigned a = 0;
+      for (int sc = 0; sc <= uc; ++sc) {
+        const int es = P * sr + 2 * (P - 1) - sc;
+        if (es < 0) break;
+        if (es > eu) continue;
+        const int base = T::col_off(es) + E - sc;           // byte of Delta(eu, es, A) with A = E - sc >= -(3p-3)
+        const uint32_t *dw = reinterpret_cast<const uint32_t *>(dsl) + (base >> 2);
+        const unsigned sel = (unsigned)(base & 3);
+        const unsigned perm = (sel == 0) ? 0x3210u : (sel == 1) ? 0x4321u : (sel == 2) ? 0x5432u : 0x6543u;
+        const uint32_t *Rc = Rs + rcolw(sc);
+        const int nw = (sc >> 2) + 1;
+        uint32_t lo = dw[0];
+        for (int k = 0; k < nw; ++k) {
+          const uint32_t hi = dw[k + 1];
+          a = __dp4a(__byte_perm(lo, hi, perm), Rc[k], a);
+          lo = hi;
+        }
+      }
+      acc[tet(ur) + f] += (int)a;
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+  bool any = false;
+  for (int i = tid; i < Pr::ld; i += nthreads) {
+    const int v = acc[i] % P;
+    gn[i] = (uint8_t)v;
+    any |= v != 0;
+  }
+  return any;
+}
+
+__host__ __device__ inline int theta_ring_words_for(int p) {
+  switch (p) {
+    case 3: return theta_ring_words<3>();
+    case 5: return theta_ring_words<5>();
+    case 7: return theta_ring_words<7>();
+    default: return 0;
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ one quartic
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code (thread 0 writes it).
 template <int P, int FORM, bool DEBUG>
@@ -435,7 +585,11 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   // A6 + A7
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
-    const bool any = theta_step<P>(delta, sm, g, g2);
+    bool any;
+    if constexpr (theta_in_smem<P>())
+      any = theta_step_smem<P>(nxt, sm, g, g2, ring);
+    else
+      any = theta_step<P>(delta, sm, g, g2);
     const int nonzero = __syncthreads_or(any ? 1 : 0);
     theta_steps = h - 1;
     if (DEBUG)

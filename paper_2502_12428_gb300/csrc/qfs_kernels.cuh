@@ -7,7 +7,7 @@ namespace qfs {
 
 // Persistent launch: every CTA pulls quartics from a global atomic queue until the queue is empty.
 template <int FORM>
-__global__ void __launch_bounds__(kThreads) fused_kernel(FusedParams prm) {
+__global__ void __launch_bounds__(kThreads, 3) fused_kernel(FusedParams prm) {
   fused_body<FORM>(prm);
 }
 

@@ -26,7 +26,7 @@ constexpr size_t kControlBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // The fused persistent kernel (dp4a form), given its workspace in the fixed array instead of a cudaMalloc'd one.
-__global__ void __launch_bounds__(kThreads) noalloc_fused_kernel(FusedParams prm) { fused_body<1>(prm); }
+__global__ void __launch_bounds__(kThreads, 3) noalloc_fused_kernel(FusedParams prm) { fused_body<1>(prm); }
 
 constexpr int kMaxDev = 64;
 void *g_scratch_addr[kMaxDev];   // device address of g_noalloc_scratch on each device, set once
