@@ -42,6 +42,7 @@ struct Smem {
   uint32_t pair_mask;     // bit tri(uI)+sI set iff that pair has a nonzero tap
   int powp[kMaxP];        // c^p mod p^2
   int slot_tab[2][kMaxUparDecl + 4];  // ring word offsets of the slices a chain round reads (double buffered)
+  uint16_t chunk_tab[32 * 40];        // chain block: flat chunk index -> (column - s0) << 8 | chunk
   int64_t item;
   int flag;
   // followed in dynamic shared memory by two byte arrays of ld entries: g (current iterate) and g_next
@@ -65,7 +66,13 @@ __host__ __device__ constexpr size_t ring_offset_for(int max_ld) {
 // -4..-1) followed by the column's chunks, so output chunk c reads slot chunks c and c+1 (input words 4c-4..4c+3).
 // Outputs past a column's end come out as zero by themselves (their inputs are all padding), so no output needs a
 // bounds check outside the Delta_1 epilogue.
-constexpr int kRingBudgetSmallP = 16384;   // ring words for p <= 7 (64 KB)
+#ifndef QFS_ROUND_CHUNKS
+#define QFS_ROUND_CHUNKS 512
+#endif
+#ifndef QFS_RING_WORDS_SMALL_P
+#define QFS_RING_WORDS_SMALL_P 16384
+#endif
+constexpr int kRingBudgetSmallP = QFS_RING_WORDS_SMALL_P;   // ring words for p <= 7 (64 KB)
 constexpr int kRingBudgetLargeP = 26624;   // ring words for p >= 11 (104 KB)
 constexpr int kMaxUpar = 8;
 
@@ -80,7 +87,7 @@ __host__ __device__ inline ChainTile chain_tile(int s0, int m_out, int budget_wo
   T.stride = 4 * (T.CR + 1);
   T.slot_words = 36 * T.stride;
   const int per_slice = chunk_prefix(s_hi + 1) - chunk_prefix(s0);
-  int up = (512 + per_slice - 1) / per_slice;
+  int up = (QFS_ROUND_CHUNKS + per_slice - 1) / per_slice;
   up = max(1, min(kMaxUpar, up));
   while (up > 1 && (2 * up + 4) * T.slot_words > budget_words) --up;
   T.upar = up;
@@ -207,7 +214,8 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
   using Pr = Prime<P>;
   const int m_out = m_in + 4;
   const uint32_t mask = sm.pair_mask;
-  const bool dense = mask == 0x7FFFu;
+  // quartics with few zero (uI, sI) pairs run every pair: a zero tap costs less than a branch per pair
+  const bool dense = __popc(mask) >= 12;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int nthreads = blockDim.x;
@@ -235,6 +243,10 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
     if (threadIdx.x < kMaxUpar + 4) {
       const int u2 = s0 - 4 + (int)threadIdx.x;
       sm.slot_tab[0][threadIdx.x] = ((u2 - s0 + 4) % T.nslot) * T.slot_words;
+    }
+    for (int s = s0 + (int)threadIdx.x; s <= s_last; s += nthreads) {
+      const int base = chunk_prefix(s) - F0;
+      for (int c = 0; c < chunks_of(s); ++c) sm.chunk_tab[base + c] = (uint16_t)(((s - s0) << 8) | c);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -265,8 +277,8 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
         for (int j = 1; j < kMaxUpar; ++j)
           if (g >= pre[j]) { du = j; gbase = pre[j]; }
         const int uo = u + du;
-        int s, c;
-        decode_chunk(g - gbase + F0, s, c);
+        const int sc_packed = sm.chunk_tab[g - gbase];
+        const int s = s0 + (sc_packed >> 8), c = sc_packed & 0xFF;
         int acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)

@@ -5,9 +5,12 @@
 
 namespace qfs {
 
+#ifndef QFS_MIN_CTAS_PER_SM
+#define QFS_MIN_CTAS_PER_SM 3
+#endif
 // Persistent launch: every CTA pulls quartics from a global atomic queue until the queue is empty.
 template <int FORM>
-__global__ void __launch_bounds__(kThreads, 3) fused_kernel(FusedParams prm) {
+__global__ void __launch_bounds__(kThreads, QFS_MIN_CTAS_PER_SM) fused_kernel(FusedParams prm) {
   fused_body<FORM>(prm);
 }
 
