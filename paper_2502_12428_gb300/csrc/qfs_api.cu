@@ -83,6 +83,7 @@ int ensure_workspace(DeviceState &S, size_t bytes) {
 cudaError_t form_occupancy(int form, int *blocks, size_t smem) {
   switch (form) {
     case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::occupancy(blocks, smem);
     default: return FormLauncher<1>::occupancy(blocks, smem);
   }
 }
@@ -90,6 +91,7 @@ cudaError_t form_occupancy(int form, int *blocks, size_t smem) {
 cudaError_t form_fused(int form, const FusedParams &prm, int grid, size_t smem, cudaStream_t st) {
   switch (form) {
     case QFS_FORM_INT32: return FormLauncher<0>::fused(prm, grid, smem, st);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::fused(prm, grid, smem, st);
     default: return FormLauncher<1>::fused(prm, grid, smem, st);
   }
 }
@@ -98,11 +100,12 @@ cudaError_t form_debug(int form, int p, const uint8_t *f, int max_h, int8_t *h_o
                        uint32_t *status, DebugPtrs dbg, cudaStream_t st) {
   switch (form) {
     case QFS_FORM_INT32: return FormLauncher<0>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
     default: return FormLauncher<1>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
   }
 }
 
-bool form_supported(int form) { return form == QFS_FORM_INT32 || form == QFS_FORM_DP4A; }
+bool form_supported(int form) { return form == QFS_FORM_INT32 || form == QFS_FORM_DP4A || form == QFS_FORM_INT8TC; }
 
 // Default workspace budget: a quarter of device memory.
 size_t default_budget(const DeviceState &S) { return S.total_mem / 4; }
@@ -251,7 +254,7 @@ int qfs_plan_prepare(int p, int64_t n_hint) {
   if (rc) return rc;
   Plan plan;
   int64_t n = n_hint > 0 ? n_hint : (int64_t)1 << 40;
-  for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A}) {
+  for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A, QFS_FORM_INT8TC}) {
     rc = make_plan(*S, form, p, n, nullptr, plan);
     if (rc) return rc;
   }

@@ -1,0 +1,5 @@
+// Parity hook kernels of the int32 form (one quartic, every intermediate array written out).
+#include "qfs_kernels.cuh"
+namespace qfs {
+QFS_DEFINE_DEBUG_LAUNCHER(0)
+}

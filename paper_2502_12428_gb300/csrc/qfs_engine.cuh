@@ -207,6 +207,48 @@ __device__ __forceinline__ void item_pairs(const uint32_t *sb0, const uint32_t *
 
 }  // namespace detail
 
+// ------------------------------------------------------------------------------------------------ int8 tensor form
+// One product of the chain as int8 tensor-core contractions: mma.sync m16n8k32 (u8 x u8 -> s32).  A tile is 16
+// output columns (rows m) x 8 consecutive outputs t0 .. t0+7 (columns n) of one output slice.  The K dimension is
+// 16 groups of four 32-bit words, group pi = tap pair (uI, sI) (the 16th group is empty): word j of group pi is
+// input word t0/4 - 1 + j of column s - sI in slice u - uI (j = 3 carries no taps), so every A fragment register
+// is one aligned shared-memory word -- no byte shuffling.  B is the Toeplitz of f's taps,
+// B[k][n] = a(uI, sI, n + 4 - 4j - i) for byte i of word j (zero outside 0..sI), fixed per quartic.  A tile executes
+// 16 x 8 x 256 MACs for 16 x 8 x 35 useful ones; accumulation is exact in int32 (at most 35 products per output).
+__device__ __forceinline__ void mma_u8_16832(int (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                             uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// (uI, sI) of tap pair pi (pi = tri(uI) + sI), pi in [0, 15)
+__host__ __device__ constexpr int pair_u(int pi) { return pi >= 10 ? 4 : pi >= 6 ? 3 : pi >= 3 ? 2 : pi >= 1 ? 1 : 0; }
+__host__ __device__ constexpr int pair_s(int pi) { return pi - tri(pair_u(pi)); }
+
+// B fragment registers of this thread (lane): b[2*kk] = rows 32kk + 4 tig .. +3, b[2*kk+1] = rows 32kk+16+4tig ..,
+// column n = group.
+__device__ __forceinline__ void tc_b_fragments(const Smem &sm, uint32_t (&b)[16]) {
+  const int lane = threadIdx.x & 31, group = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int pi = 2 * kk + h;
+      uint32_t w = 0;
+      if (pi < 15 && tig < 3) {
+        const int uI = pair_u(pi), sI = pair_s(pi);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int tI = group + 4 - 4 * tig - i;
+          if (tI >= 0 && tI <= sI) w |= (uint32_t)sm.taps[tet(uI) + tri(sI) + tI] << (8 * i);
+        }
+      }
+      b[2 * kk + h] = w;
+    }
+}
+
 template <int P, int FORM, bool LAST, bool DEBUG>
 __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
                                            Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
@@ -220,6 +262,8 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
   const int nwarps = blockDim.x >> 5;
   const int nthreads = blockDim.x;
   bool bad = false;
+  uint32_t tcb[16];
+  if (FORM == 2) tc_b_fragments(sm, tcb);
   for (int s0 = 0; s0 <= m_out; s0 += 32) {
     const ChainTile T = chain_tile(s0, m_out, ring_budget(P));
     const int s_last = min(s0 + 31, m_out);
@@ -269,6 +313,76 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
       }
       const int total = pre[kMaxUpar];
       const int *stab = sm.slot_tab[tab];
+      if (FORM == 2) {
+        // tiles: (slice du, column group of 16, word pair wp); word pairs of a group cover its longest column
+        int tpre[2 * kMaxUpar + 1];
+        tpre[0] = 0;
+#pragma unroll
+        for (int i = 0; i < 2 * kMaxUpar; ++i) {
+          const int du = i >> 1, grp = i & 1;
+          const int hi = min(s_last, u + du);
+          const int sg = s0 + 16 * grp;
+          tpre[i + 1] = tpre[i] + ((du < nU && sg <= hi) ? 2 * chunks_of(min(hi, sg + 15)) : 0);
+        }
+        const int ntiles = tpre[2 * kMaxUpar];
+        const int group = lane >> 2, tig = lane & 3;
+        const int joff = tig < 3 ? tig : 2;  // word j = 3 carries no taps: reload word 2
+        for (int tile = warp; tile < ntiles; tile += nwarps) {
+          int i = 0, tbase = 0;
+#pragma unroll
+          for (int k2 = 1; k2 < 2 * kMaxUpar; ++k2)
+            if (tile >= tpre[k2]) { i = k2; tbase = tpre[k2]; }
+          const int du = i >> 1, grp = i & 1, wp = tile - tbase;
+          const int uo = u + du;
+          const int hi = min(s_last, uo);
+          const int sg = s0 + 16 * grp;
+          int acc[4] = {0, 0, 0, 0};
+          const int rbase_a = (sg - s0 + group + 4) * T.stride + 2 * wp + 3 + joff;
+          const int rbase_b = rbase_a + 8 * T.stride;
+          int sb[5];
+#pragma unroll
+          for (int uI = 0; uI < 5; ++uI) sb[uI] = stab[du + 4 - uI];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int p0 = 2 * kk, p1 = 2 * kk + 1;
+            const int o0 = sb[pair_u(p0)] - pair_s(p0) * T.stride;
+            const int o1 = p1 < 15 ? sb[pair_u(p1)] - pair_s(p1) * T.stride : sb[0];
+            const uint32_t a0 = ring[o0 + rbase_a], a1 = ring[o0 + rbase_b];
+            const uint32_t a2 = ring[o1 + rbase_a], a3 = ring[o1 + rbase_b];
+            mma_u8_16832(acc, a0, a1, a2, a3, tcb[2 * kk], tcb[2 * kk + 1]);
+          }
+          // acc: rows group (c0, c1) and group + 8 (c2, c3), outputs t = 8 wp + 2 tig + {0, 1}
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int s = sg + group + 8 * h;
+            uint32_t half = 0, ghalf = 0;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              int G = acc[2 * h + e] % Pr::p2;
+              const int t = 8 * wp + 2 * tig + e;
+              if (LAST) {
+                if (DEBUG) ghalf |= (uint32_t)G << (8 * e);
+                if (t <= s && (uo % P) == 0 && (s % P) == 0 && (t % P) == 0) {
+                  const int J = tet(uo / P) + tri(s / P) + t / P;
+                  G = G - sm.powp[gs[J]];
+                  if (G < 0) G += Pr::p2;
+                }
+                if (s <= hi && G % P) bad = true;
+                G /= P;
+              }
+              half |= (uint32_t)G << (8 * e);
+            }
+            const uint32_t other = __shfl_down_sync(0xffffffffu, half, 1);
+            const uint32_t gother = __shfl_down_sync(0xffffffffu, ghalf, 1);
+            const int w = 2 * wp + (tig >> 1);
+            if ((tig & 1) == 0 && s <= hi && w < 4 * chunks_of(s)) {
+              const int o = sm.SW[uo] + colw(s) + w;
+              out[o] = half | (other << 16);
+              if (DEBUG && LAST) dbg.G[o] = ghalf | (gother << 16);
+            }
+          }
+        }
+      } else
       for (int it = warp; it * 32 < total; it += nwarps) {
         const int g = it * 32 + lane;
         if (g >= total) continue;

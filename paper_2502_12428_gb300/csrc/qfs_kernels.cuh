@@ -58,7 +58,9 @@ struct FormLauncher {
                                          (int)smem);                                                          \
     if (e != cudaSuccess) return e;                                                                           \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<FORM>, kThreads, smem);  \
-  }                                                                                                           \
+  }
+
+#define QFS_DEFINE_DEBUG_LAUNCHER(FORM)                                                                       \
   template <>                                                                                                 \
   cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st) {   \

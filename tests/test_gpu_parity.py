@@ -12,7 +12,7 @@ from paper_2502_12428_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-CORE_FORMS = ["int32", "dp4a"]
+CORE_FORMS = ["int32", "dp4a", "int8tc"]
 
 
 @pytest.fixture(scope="session")
@@ -71,7 +71,7 @@ def test_stages_p5(qfs, form):
 
 @pytest.mark.slow
 def test_stages_p7(qfs):
-    row = next(r[3] for r in example_quartics() if r[0] == 7 and r[1] == 2)
+    row = next(r[3] for r in example_quartics() if r[0] == 7 and r[1] == 2)  # one quartic, every form
     ref = oracle.stage_arrays_a(7, row)
     for form in CORE_FORMS:
         got = qfs.debug_stages(7, dev_tensor(row), form=form)
@@ -136,6 +136,7 @@ def test_full_size_dense(qfs, cfg):
     ft = dev_tensor(f)
     got = {form: qfs.heights(p, ft, form=form).cpu().numpy() for form in CORE_FORMS}
     assert np.array_equal(got["int32"], got["dp4a"])
+    assert np.array_equal(got["int8tc"], got["dp4a"])
     h = got["dp4a"]
     assert h.min() >= 0 and h.max() <= 10
     checked = sampled_check(qfs, p, f, h, seed=cfg)
