@@ -62,7 +62,8 @@ enum {
 /* Engines: how the per-quartic stages are scheduled. */
 enum {
   QFS_ENGINE_FUSED = 0,   /* one persistent launch, work stealing over quartics, every stage fused per quartic */
-  QFS_ENGINE_STAGED = 1   /* one kernel per stage (power, Delta_1, theta, test) over batches of survivors */
+  QFS_ENGINE_STAGED = 1   /* one kernel per stage (Fedder test, power, Delta_1, theta, test) over chunks of
+                             quartics; dp4a form only; the groups of a multi call run one after another */
 };
 
 #define QFS_MAX_GROUPS 8

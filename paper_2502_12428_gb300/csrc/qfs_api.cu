@@ -10,6 +10,7 @@
 
 #include "../../include/qfs.h"
 #include "qfs_kernels.cuh"
+#include "qfs_staged.cuh"
 
 namespace qfs {
 
@@ -22,7 +23,9 @@ struct DeviceState {
   size_t total_mem = 0;
   void *ws = nullptr;          // persistent-CTA workspaces
   size_t ws_bytes = 0;
-  void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32)
+  void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32), [16]: stats (2 x u64)
+  void *staged = nullptr;      // staged-engine survivor buffers
+  size_t staged_bytes = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -80,6 +83,71 @@ int ensure_workspace(DeviceState &S, size_t bytes) {
   return QFS_OK;
 }
 
+// Default workspace budget: a quarter of device memory.
+size_t default_budget(const DeviceState &S) { return S.total_mem / 4; }
+
+int ensure_staged(DeviceState &S, size_t bytes) {
+  if (S.staged_bytes >= bytes) return QFS_OK;
+  if (S.staged) {
+    cudaError_t e = cudaFree(S.staged);
+    S.staged = nullptr;
+    S.staged_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (cudaMalloc(&S.staged, bytes) != cudaSuccess) {
+    S.staged = nullptr;
+    (void)cudaGetLastError();
+    return QFS_ERR_NO_MEMORY;
+  }
+  S.staged_bytes = bytes;
+  return QFS_OK;
+}
+
+// Staged engine: one group after another, each in chunks whose survivor buffers fit the budget.
+int run_staged(DeviceState &S, const FusedParams &prm, const qfs_options_t *opts, cudaStream_t stream) {
+  for (int gi = 0; gi < prm.n_groups; ++gi) {
+    const FusedGroup &g = prm.g[gi];
+    const int p = g.p;
+    StagedPlan pl;
+    pl.sms = S.sms;
+    int blocks = 0;
+    cudaError_t e = staged_occupancy(p, &blocks);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int64_t grid = (int64_t)S.sms * std::max(1, opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : blocks);
+    if (opts && opts->max_ctas > 0) grid = std::min<int64_t>(grid, opts->max_ctas);
+    pl.ws_words = (size_t)padded_words(4 * p * (p - 1));
+    const size_t per_cta = 2 * pl.ws_words * sizeof(uint32_t);
+    const size_t budget = opts && opts->workspace_budget ? opts->workspace_budget : default_budget(S);
+    grid = std::min<int64_t>(grid, (int64_t)(budget / 2 / per_cta));
+    if (grid < 1) return QFS_ERR_NO_MEMORY;
+    pl.grid = (int)grid;
+    int rc = ensure_workspace(S, (size_t)grid * per_cta);
+    if (rc) return rc;
+    const size_t per_surv = staged_survivor_bytes(p);
+    int64_t chunk = std::min<int64_t>({g.n, (int64_t)8192, (int64_t)((budget / 2) / per_surv)});
+    if (chunk < 1) return QFS_ERR_NO_MEMORY;
+    const int ld = tet(4 * (p - 1) + 1);
+    const size_t gbytes = (size_t)chunk * pl.ws_words * 4;
+    const size_t need = 256 + gbytes + 2 * (size_t)chunk * ld + (size_t)chunk * 4 + (size_t)chunk + 64;
+    rc = ensure_staged(S, need);
+    if (rc) return rc;
+    char *b = static_cast<char *>(S.staged);
+    pl.counters = reinterpret_cast<unsigned *>(b);
+    pl.G = reinterpret_cast<uint32_t *>(b + 256);
+    pl.gA = reinterpret_cast<uint8_t *>(b + 256 + gbytes);
+    pl.gB = pl.gA + (size_t)chunk * ld;
+    pl.rows = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(pl.gB + (size_t)chunk * ld) + 15) & ~uintptr_t(15));
+    pl.active = reinterpret_cast<uint8_t *>(pl.rows + chunk);
+    pl.chunk = chunk;
+    pl.ws = reinterpret_cast<uint32_t *>(S.ws);
+    pl.stats = reinterpret_cast<unsigned long long *>(static_cast<char *>(S.ctrl) + 16);
+    pl.status = reinterpret_cast<uint32_t *>(static_cast<char *>(S.ctrl) + 8);
+    e = staged_run(pl, p, g.coeffs, g.heights, g.n, prm.max_h, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return QFS_OK;
+}
+
 cudaError_t form_occupancy(int form, int *blocks, size_t smem) {
   switch (form) {
     case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem);
@@ -107,8 +175,6 @@ cudaError_t form_debug(int form, int p, const uint8_t *f, int max_h, int8_t *h_o
 
 bool form_supported(int form) { return form == QFS_FORM_INT32 || form == QFS_FORM_DP4A || form == QFS_FORM_INT8TC; }
 
-// Default workspace budget: a quarter of device memory.
-size_t default_budget(const DeviceState &S) { return S.total_mem / 4; }
 
 struct Plan {
   int grid = 0;
@@ -186,7 +252,8 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   }
   int form = opts && opts->form >= 0 ? opts->form : g_default_form;
   int engine = opts && opts->engine >= 0 ? opts->engine : QFS_ENGINE_FUSED;
-  if (!form_supported(form) || engine != QFS_ENGINE_FUSED) return QFS_ERR_FORM;
+  if (!form_supported(form) || (engine != QFS_ENGINE_FUSED && engine != QFS_ENGINE_STAGED)) return QFS_ERR_FORM;
+  if (engine == QFS_ENGINE_STAGED && form != QFS_FORM_DP4A) return QFS_ERR_FORM;
   if (n_items == 0) return QFS_OK;
 
   std::lock_guard<std::mutex> lock(g_mu);
@@ -217,6 +284,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   prm.n_items = n_items;
   prm.max_h = max_h;
   prm.sw_len = 4 * max_p * (max_p - 1) + 2;
+  if (engine == QFS_ENGINE_STAGED) return run_staged(*S, prm, opts, stream);
 
   Plan plan;
   rc = make_plan(*S, form, max_p, n_items, opts, plan);
@@ -273,6 +341,7 @@ int qfs_shutdown(void) {
     if (cudaSetDevice(d) != cudaSuccess) { rc = QFS_ERR_CUDA; continue; }
     if (S.ws && cudaFree(S.ws) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.ctrl && cudaFree(S.ctrl) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.staged && cudaFree(S.staged) != cudaSuccess) rc = QFS_ERR_CUDA;
     S = DeviceState();
   }
   cudaSetDevice(cur);

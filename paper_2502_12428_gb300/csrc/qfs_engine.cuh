@@ -627,21 +627,18 @@ __host__ __device__ inline int theta_ring_words_for(int p) {
 
 // ------------------------------------------------------------------------------------------------ one quartic
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code (thread 0 writes it).
-template <int P, int FORM, bool DEBUG>
-__device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
-                               uint32_t *ring, uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg,
-                               int &theta_steps) {
+// A1: read the 35 coefficients into the tap tables; returns false (after a barrier) if one is >= p.
+template <int P>
+__device__ __forceinline__ bool setup_quartic(const uint8_t *__restrict__ f35, Smem &sm) {
   using Pr = Prime<P>;
   const int tid = threadIdx.x;
-  theta_steps = 0;
-  // A1: coefficients, validation, tap tables
   int bad = 0;
   if (tid < 35) {
     const int a = f35[tid];
     bad = a >= P;
     sm.taps[tid] = a;
   }
-  if (__syncthreads_or(bad)) return -1;
+  if (__syncthreads_or(bad)) return false;
   if (tid == 0) {
     uint32_t mask = 0;
     for (int uI = 0; uI <= 4; ++uI)
@@ -663,6 +660,16 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
       sm.powp[c] = v;
     }
   }
+  return true;
+}
+
+// A2 + A3: f into bufA, the chain to f~^(p-1) mod p^2, and g = f^(p-1) mod p (packed) into gs.  Returns the
+// buffer holding f~^(p-1); gs[witness] != 0 means height 1 (read after the closing barrier).
+template <int P, int FORM, bool DEBUG>
+__device__ __forceinline__ uint32_t *power_to_g(Smem &sm, uint8_t *gs, uint32_t *ring, uint32_t *bufA,
+                                                uint32_t *bufB, uint32_t *status, DebugPtrs dbg) {
+  using Pr = Prime<P>;
+  const int tid = threadIdx.x;
   // f into bufA (padded, degree 4: every column is one chunk)
   for (int k = tid; k < sm.SW[5] / 4; k += blockDim.x) {
     int u, s, c;
@@ -672,7 +679,6 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
     *reinterpret_cast<uint4 *>(bufA + 4 * k) = make_uint4(words[0], words[1], words[2], words[3]);
   }
   __syncthreads();
-  // A2: f~^(k+1) = f~^k * f~ for k = 1 .. p-2
   uint32_t *cur = bufA, *nxt = bufB;
   int m = 4;
   for (int k = 1; k <= P - 2; ++k) {
@@ -681,7 +687,6 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
     uint32_t *t = cur; cur = nxt; nxt = t;
     m += 4;
   }
-  // A3: g = f^(p-1) mod p into shared memory (packed); witness test
   for (int k = tid; k < sm.SW[Pr::d + 1] / 4; k += blockDim.x) {
     int u, s, c;
     decode_form_chunk(k, Pr::d, sm.SW, u, s, c);
@@ -693,30 +698,63 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
     }
   }
   __syncthreads();
-  if (DEBUG)
-    for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.g[i] = gs[i];
-  if (gs[Pr::witness] != 0) return 1;
-  // A4 + A5: chain to f~^(p(p-1)); the last product carries the Delta_1 epilogue
+  return cur;
+}
+
+// A4 (+ A5 when LAST_DELTA): the chain from f~^(p-1) in `cur` to f~^(p(p-1)); the last product goes to `last_out`.
+template <int P, int FORM, bool LAST_DELTA, bool DEBUG>
+__device__ __forceinline__ void power_to_G(Smem &sm, const uint8_t *gs, uint32_t *ring, uint32_t *cur,
+                                           uint32_t *other, uint32_t *last_out, uint32_t *status, DebugPtrs dbg) {
+  using Pr = Prime<P>;
+  uint32_t *nxt = other;
+  int m = Pr::d;
   for (int k = P - 1; k <= P * (P - 1) - 2; ++k) {
     chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
     __syncthreads();
     uint32_t *t = cur; cur = nxt; nxt = t;
     m += 4;
   }
-  chain_step<P, FORM, true, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
+  chain_step<P, FORM, LAST_DELTA, DEBUG>(cur, last_out ? last_out : nxt, m, sm, ring, gs, status, dbg);
   __syncthreads();
+}
+
+// One theta step on g (shared) into gn (shared), Delta in global memory (padded, degree D).  Returns whether some
+// output is nonzero (same value in every thread).
+template <int P>
+__device__ __forceinline__ bool theta_any(const uint32_t *delta, Smem &sm, const uint8_t *g, uint8_t *gn,
+                                          uint32_t *ring) {
+  bool any;
+  if constexpr (theta_in_smem<P>())
+    any = theta_step_smem<P>(delta, sm, g, gn, ring);
+  else
+    any = theta_step<P>(reinterpret_cast<const uint8_t *>(delta), sm, g, gn);
+  return __syncthreads_or(any ? 1 : 0) != 0;
+}
+
+// Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code.
+template <int P, int FORM, bool DEBUG>
+__device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
+                               uint32_t *ring, uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg,
+                               int &theta_steps) {
+  using Pr = Prime<P>;
+  const int tid = threadIdx.x;
+  theta_steps = 0;
+  if (!setup_quartic<P>(f35, sm)) return -1;
+  uint32_t *cur = power_to_g<P, FORM, DEBUG>(sm, gs, ring, bufA, bufB, status, dbg);
+  uint32_t *other = cur == bufA ? bufB : bufA;
   if (DEBUG)
-    for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = nxt[k];
-  const uint8_t *delta = reinterpret_cast<const uint8_t *>(nxt);
+    for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.g[i] = gs[i];
+  if (gs[Pr::witness] != 0) return 1;
+  // A4 + A5 into `other` or `cur`, whichever the chain's parity leaves last
+  constexpr int nsteps = P * (P - 1) - (P - 1);   // products from f~^(p-1) to f~^(p(p-1))
+  uint32_t *delta = (nsteps % 2) ? other : cur;
+  power_to_G<P, FORM, true, DEBUG>(sm, gs, ring, cur, other, nullptr, status, dbg);
+  if (DEBUG)
+    for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
   // A6 + A7
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
-    bool any;
-    if constexpr (theta_in_smem<P>())
-      any = theta_step_smem<P>(nxt, sm, g, g2, ring);
-    else
-      any = theta_step<P>(delta, sm, g, g2);
-    const int nonzero = __syncthreads_or(any ? 1 : 0);
+    const bool nonzero = theta_any<P>(delta, sm, g, g2, ring);
     theta_steps = h - 1;
     if (DEBUG)
       for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = g2[i];

@@ -225,3 +225,31 @@ def test_determinism_across_cta_counts(qfs):
 
 def test_device_status_clean(qfs):
     assert qfs.read_status() == 0
+
+
+# ------------------------------------------------------------------------------------- staged engine
+@pytest.mark.parametrize("p,n", [(3, 500), (5, 3000), (7, 600)])
+def test_staged_engine_matches_fused_and_oracle(qfs, p, n):
+    f = np.concatenate([inputs.dense(p, n, 9100 + p), inputs.sparse(p, n // 2, 9200 + p)])
+    bad = f.copy()
+    bad[1, 3] = p
+    t = dev_tensor(bad)
+    fused = qfs.heights(p, t).cpu().numpy()
+    staged = qfs.heights(p, t, engine="staged").cpu().numpy()
+    assert np.array_equal(staged, fused)
+    want = oracle.heights(p, f)
+    want[1] = -1
+    assert np.array_equal(staged, want)
+    for max_h in (1, 3):
+        assert np.array_equal(qfs.heights(p, t, engine="staged", max_h=max_h).cpu().numpy(),
+                              qfs.heights(p, t, max_h=max_h).cpu().numpy())
+
+
+def test_staged_engine_small_chunks_and_multi(qfs):
+    # a tiny workspace budget forces many chunks (admission by memory)
+    f5 = inputs.dense(5, 5000, 9300)
+    f7 = inputs.dense(7, 400, 9301)
+    t5, t7 = dev_tensor(f5), dev_tensor(f7)
+    outs = qfs.heights_multi([(5, t5, None), (7, t7, None)], engine="staged", workspace_budget=64 << 20)
+    assert np.array_equal(outs[0].cpu().numpy(), oracle.heights(5, f5))
+    assert np.array_equal(outs[1].cpu().numpy(), oracle.heights(7, f7))
