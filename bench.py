@@ -153,6 +153,19 @@ def config_batch(cfg, rank=0):
     return p, n, kind, gen(p, n, seed, row0=rank * n)
 
 
+def mixed_batch(rank=0):
+    """Mixed-prime workload: 131,072 quartics at p = 5, 131,072 at p = 7 and 4,096 at p = 11, each followed by its
+    image under a random PGL_4(F_p) change of variables (so every group holds 2n rows)."""
+    groups, total = [], 0
+    seed = inputs.config_seed(5)
+    for p, n, kind in inputs.CONFIG_SIZES[5]:
+        f = inputs.dense(p, n, seed + p, row0=rank * n)
+        A = inputs.pgl4_matrices(p, n, seed + 100 + p, row0=rank * n)
+        groups.append((p, np.concatenate([f, inputs.substitute(f, A, p)])))
+        total += 2 * n
+    return groups, total
+
+
 def workload_name(cfg):
     (p, n, kind), = inputs.CONFIG_SIZES[cfg]
     return f"p{p}-{kind}-{n}"
@@ -189,10 +202,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_steps(p, coeffs, form, steps, warmup):
+    def timed_steps(p, coeffs, form, steps, warmup, engine=None):
         out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=dev)
         for _ in range(warmup):
-            qfs.heights(p, coeffs, out=out, form=form)
+            qfs.heights(p, coeffs, out=out, form=form, engine=engine)
         torch.cuda.synchronize()
         qfs.read_stats()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -201,7 +214,7 @@ def run_ours(args):
         for i in range(steps):
             flush.fill_(i & 0xFF)                # L2 flush between timed steps, outside the events
             ev[i][0].record(stream)
-            qfs.heights(p, coeffs, out=out, form=form)
+            qfs.heights(p, coeffs, out=out, form=form, engine=engine)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -260,6 +273,42 @@ def run_ours(args):
         ms5 = max_over_ranks(statistics.mean(per5))
         second[form] = {"value": round(world * n5 / (ms5 / 1e3), 1), "ms_per_step": round(ms5, 3)}
 
+    # the other workloads, each timed in the headline form: sparse p = 5 (uneven work) and the mixed-prime batch
+    # with PGL_4 images in one launch; and the staged engine on the headline workload
+    extra = {}
+    if not args.no_extra:
+        p3, n3, kind3, f3 = config_batch(3, rank)
+        c3 = torch.from_numpy(f3).to(dev)
+        o3, per3, s3, t3 = timed_steps(p3, c3, args.form, max(2, args.steps // 2), args.warmup)
+        ms3 = max_over_ranks(statistics.mean(per3))
+        extra[workload_name(3)] = {"value": round(world * n3 / (ms3 / 1e3), 1), "ms_per_step": round(ms3, 3),
+                                   "past_height_1": s3, "theta_steps": t3}
+        groups5, n5tot = mixed_batch(rank)
+        dev_groups = [(p_, torch.from_numpy(f_).to(dev), None) for p_, f_ in groups5]
+        for _ in range(args.warmup):
+            qfs.heights_multi(dev_groups, form=args.form)
+        torch.cuda.synchronize()
+        barrier()
+        ev5 = []
+        for i in range(max(2, args.steps // 2)):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            outs5 = qfs.heights_multi(dev_groups, form=args.form)
+            b.record(stream)
+            ev5.append((a, b))
+        torch.cuda.synchronize()
+        ms5 = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in ev5))
+        invariant = all(np.array_equal(o.cpu().numpy()[:len(f_) // 2], o.cpu().numpy()[len(f_) // 2:])
+                        for o, (p_, f_) in zip(outs5, groups5))
+        extra["mixed-p5-p7-p11-pgl4"] = {"value": round(world * n5tot / (ms5 / 1e3), 1), "ms_per_step": round(ms5, 3),
+                                         "quartics": n5tot, "pgl4_invariant": bool(invariant)}
+        os_, per_s, ss, ts = timed_steps(p, coeffs, "dp4a", 2, args.warmup, engine="staged")
+        extra[workload_name(HEADLINE_CFG) + " staged engine"] = {
+            "value": round(world * n / (max_over_ranks(statistics.mean(per_s)) / 1e3), 1),
+            "ms_per_step": round(max_over_ranks(statistics.mean(per_s)), 3),
+            "bit_exact_vs_fused": bool(np.array_equal(os_.cpu().numpy(), heights_np))}
+
     # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step
     host_in = torch.from_numpy(f_np).pin_memory()
     host_out = torch.empty(n, dtype=torch.int8).pin_memory()
@@ -296,7 +345,7 @@ def run_ours(args):
                        "coefficients": "uniform in F_7, splitmix64 seed 0x5EED0004", "max_h": 10,
                        "form": args.form, "engine": "fused persistent", "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{world}"},
-            "forms": forms_out, "second_workload": second,
+            "forms": forms_out, "second_workload": second, "other_workloads": extra,
             "heights_histogram": {"invalid": int(hist[0]), "inf": int(hist[1]),
                                   **{str(h): int(hist[h + 1]) for h in range(1, 11)}},
             "work_per_step": {"past_height_1": surv, "theta_steps": theta, "algorithmic_macs": macs},
@@ -367,9 +416,10 @@ def run_ncu_case(args):
     p, n, kind, f_np = config_batch(HEADLINE_CFG, 0)
     coeffs = torch.from_numpy(f_np[:args.ncu_quartics]).cuda()
     for _ in range(2):
-        h = qfs.heights(p, coeffs, form=args.form, max_ctas=args.ncu_ctas)
+        h = qfs.heights(p, coeffs, form=args.form, max_ctas=args.ncu_ctas, engine=args.engine)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": workload_name(HEADLINE_CFG), "quartics": args.ncu_quartics, "form": args.form,
+                      "engine": args.engine or "fused",
                       "past_height_1": int((h.cpu().numpy() != 1).sum())}))
 
 
@@ -384,9 +434,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="quartics per oracle run (default 256 for the baseline leg, 128 per reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the sparse, mixed-prime and staged-engine lines")
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-quartics", type=int, default=8192)
     ap.add_argument("--ncu-ctas", type=int, default=0)
+    ap.add_argument("--engine", choices=["fused", "staged"], default=None, help="engine of the --ncu-case launch")
     args = ap.parse_args()
     args.forms = args.forms.split(",")
     if args.cpu_sample is None:

@@ -145,14 +145,69 @@ def _mul_table(a, b):
 def _form_mul(X, a, Y, b, p, tables):
     key = (a, b)
     if key not in tables:
-        tables[key] = _mul_table(a, b)
+        tables[key] = _mul_table(a, b).astype(np.float64)
     n = X.shape[0]
-    outer = (X[:, :, None] * Y[:, None, :]).reshape(n, -1)
-    return (outer @ tables[key]) % p
+    outer = (X[:, :, None] * Y[:, None, :]).reshape(n, -1).astype(np.float64)
+    # entries are below p^2 and a product sums at most 35 of them: float64 (BLAS) is exact here
+    return np.rint(outer @ tables[key]).astype(np.int64) % p
+
+
+def _eval_points(p):
+    """35 points of F_p^4 on which the quartic monomials are linearly independent mod p (p >= 5: a quartic has
+    every partial degree below p, so it is determined by its values), with the inverse of their evaluation matrix."""
+    rng = np.random.default_rng(1000 + p)
+    while True:
+        pts = rng.integers(0, p, (35, 4))
+        V = np.array([[int(np.prod([int(x) ** e for x, e in zip(pt, m)])) % p for m in MONOMIALS] for pt in pts])
+        inv = _inv_mod(V, p)
+        if inv is not None:
+            return pts, inv
+
+
+def _inv_mod(V, p):
+    n = V.shape[0]
+    M = np.concatenate([V % p, np.eye(n, dtype=np.int64)], axis=1).astype(np.int64)
+    for c in range(n):
+        piv = next((r for r in range(c, n) if M[r, c] % p), None)
+        if piv is None:
+            return None
+        M[[c, piv]] = M[[piv, c]]
+        M[c] = (M[c] * pow(int(M[c, c]), -1, p)) % p
+        for r in range(n):
+            if r != c and M[r, c]:
+                M[r] = (M[r] - M[r, c] * M[c]) % p
+    return M[:, n:]
+
+
+_POINTS = {}
 
 
 def substitute(coeffs, A, p):
     """f(A x) for each row: x_j -> sum_k A[j,k] x_k, expanded and reduced mod p.  Returns uint8 (n, 35)."""
+    if p >= 5:
+        # evaluate f at A x_m for 35 fixed points x_m and interpolate: h = V^-1 (f(A x_m))_m mod p
+        if p not in _POINTS:
+            _POINTS[p] = _eval_points(p)
+        pts, inv = _POINTS[p]
+        coeffs = np.asarray(coeffs, dtype=np.float64).reshape(-1, 35)
+        A = np.asarray(A, dtype=np.int64)
+        E = np.array(MONOMIALS)                                   # (35, 4) exponents
+        out = np.empty((coeffs.shape[0], 35), np.uint8)
+        for r0 in range(0, coeffs.shape[0], 8192):
+            Y = (np.einsum("njk,mk->nmj", A[r0:r0 + 8192], pts) % p).astype(np.float64)   # (c, 35 points, 4)
+            Yt = np.moveaxis(Y, -1, 0).reshape(4, -1)                                       # (4, c*35)
+            pw = np.stack([np.ones_like(Yt), Yt, Yt ** 2, Yt ** 3, Yt ** 4], axis=1)        # (4, 5, c*35)
+            # M[I, c*35] = prod_j Y_j^(I_j): entries below p^4, sums below 35 p^5 -- exact in float64
+            M = pw[0, E[:, 0]] * pw[1, E[:, 1]] * pw[2, E[:, 2]] * pw[3, E[:, 3]]
+            M = M.reshape(35, Y.shape[0], 35)                                              # (I, c, point)
+            vals = np.einsum("icm,ci->cm", M, coeffs[r0:r0 + 8192]) % p
+            out[r0:r0 + 8192] = ((vals @ inv.T.astype(np.float64)) % p).astype(np.uint8)
+        return out
+    return _substitute_expand(coeffs, A, p)
+
+
+def _substitute_expand(coeffs, A, p):
+    """f(A x) by expanding the products of the four linear forms (any p)."""
     coeffs = np.asarray(coeffs, dtype=np.int64).reshape(-1, 35)
     n = coeffs.shape[0]
     tables = {}
