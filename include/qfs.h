@@ -66,6 +66,13 @@ enum {
                              quartics; dp4a form only; the groups of a multi call run one after another */
 };
 
+/* How A4 + A5 form Delta_1(f^(p-1)) (both produce the same array, bit for bit). */
+enum {
+  QFS_POWER_CHAIN = 0,     /* Algorithm 1 literally: lift(g)^p mod p^2 as the chain f~^(p(p-1)), then (G - S) / p */
+  QFS_POWER_IDENTITY = 1   /* the exact rewriting Delta_1(f^(p-1)) = E(x^p) - f^(p-2)(x^p) Delta_1(f) mod p, from
+                              f~^p = A + p Delta_1(f) (Proposition of Sec. 3.1) and the binomial theorem mod p^2 */
+};
+
 #define QFS_MAX_GROUPS 8
 
 /* One batch of quartics over one prime (all pointers device memory owned by the caller). */
@@ -83,6 +90,7 @@ typedef struct {
   int ctas_per_sm;           /* fused engine: resident CTAs per SM, 0 = auto */
   int max_ctas;              /* cap on persistent CTAs (admission), 0 = no cap beyond memory */
   size_t workspace_budget;   /* bytes of device workspace the call may use, 0 = library default */
+  int power;                 /* QFS_POWER_*; -1 = QFS_POWER_CHAIN (fused engine only for the identity) */
 } qfs_options_t;
 
 /* Heights of n quartics over F_p.  coeffs: device, n x 35 uint8.  heights_out: device, n int8.
@@ -105,6 +113,19 @@ int qfs_set_default_form(int form);
    a fused launch over up to n_hint quartics needs (n_hint <= 0: a full-device launch).  Synchronous; it may call
    cudaMalloc.  Optional: the first qfs_heights call does the same lazily. */
 int qfs_plan_prepare(int p, int64_t n_hint);
+
+/* Chain tile shape per prime (process-wide; the autotuner below picks it on the device at hand).
+   round_chunks: target (column, 16-byte chunk) work items per round of the shared-memory sweep; ring_bytes: the
+   shared memory the slice ring may use (it bounds how many slices a round covers, and with it the occupancy).
+   qfs_tune_set(p, 0, 0) restores the built-in default.  Returns QFS_ERR_FORM for values outside
+   [32, 4096] x [4 KB, ...) and QFS_ERR_NO_MEMORY if the CTA would need more than 227 KB of shared memory. */
+int qfs_tune_set(int p, int round_chunks, size_t ring_bytes);
+int qfs_tune_get(int p, int *round_chunks, size_t *ring_bytes, size_t *smem_bytes);
+
+/* Times the fused engine on n quartics (device, n x 35) for every candidate tile shape of prime p, keeps the
+   fastest with qfs_tune_set and reports it.  Synchronous; allocates a scratch output of n bytes. */
+int qfs_autotune(int p, int64_t n, const uint8_t *coeffs, int form, int *best_round, size_t *best_ring,
+                 float *best_ms);
 
 /* Frees every workspace of every device this process used.  Synchronous. */
 int qfs_shutdown(void);
@@ -146,7 +167,8 @@ int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int max_h, int8
      G_out     C(4p(p-1)+3,3) values: f~^(p(p-1)) mod p^2 (equal to lift(g)^p mod p^2), only if height != 1
      delta_out C(4p(p-1)+3,3) values: Delta_1(f^(p-1)) mod p, only if height != 1
      iters_out (max_h-1) x C(4p-1,3): row h-2 = the iterate g_h, for the rows computed
-   height_out: device, 1 int8 (the same code qfs_heights writes).  Synchronous. */
+   height_out: device, 1 int8 (the same code qfs_heights writes).  form = QFS_FORM_* | (QFS_POWER_* << 8); with the
+   identity power mode G_out is left untouched (that route never forms G).  Synchronous. */
 int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
                      int32_t *delta_out, int32_t *iters_out, int8_t *height_out);
 

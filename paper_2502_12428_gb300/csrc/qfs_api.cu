@@ -32,6 +32,12 @@ constexpr int kMaxDevices = 64;
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
 int g_default_form = QFS_FORM_DP4A;
+TileConfig g_tile[kMaxP + 1];   // per-prime chain tile shape (0 = not set: defaults)
+
+TileConfig tile_for(int p) {
+  const TileConfig t = g_tile[p];
+  return t.round_chunks > 0 ? t : default_tile(p);
+}
 int g_last_cuda = 0;
 
 bool valid_p(int p) { return p == 3 || p == 5 || p == 7 || p == 11 || p == 13; }
@@ -165,11 +171,11 @@ cudaError_t form_fused(int form, const FusedParams &prm, int grid, size_t smem, 
 }
 
 cudaError_t form_debug(int form, int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *A, uint32_t *B,
-                       uint32_t *status, DebugPtrs dbg, cudaStream_t st) {
+                       uint32_t *status, DebugPtrs dbg, cudaStream_t st, int power_mode) {
   switch (form) {
-    case QFS_FORM_INT32: return FormLauncher<0>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
-    case QFS_FORM_INT8TC: return FormLauncher<2>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
-    default: return FormLauncher<1>::debug(p, f, max_h, h_out, A, B, status, dbg, st);
+    case QFS_FORM_INT32: return FormLauncher<0>::debug(p, f, max_h, h_out, A, B, status, dbg, st, power_mode);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::debug(p, f, max_h, h_out, A, B, status, dbg, st, power_mode);
+    default: return FormLauncher<1>::debug(p, f, max_h, h_out, A, B, status, dbg, st, power_mode);
   }
 }
 
@@ -182,8 +188,9 @@ struct Plan {
   size_t ws_words = 0;
 };
 
-int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_options_t *opts, Plan &plan) {
-  plan.smem = smem_bytes_for(max_p);
+int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_options_t *opts, Plan &plan,
+              size_t smem) {
+  plan.smem = smem;
   plan.ws_words = (size_t)padded_words(4 * max_p * (max_p - 1));
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
   if (per_sm == 0) {
@@ -253,7 +260,9 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   int form = opts && opts->form >= 0 ? opts->form : g_default_form;
   int engine = opts && opts->engine >= 0 ? opts->engine : QFS_ENGINE_FUSED;
   if (!form_supported(form) || (engine != QFS_ENGINE_FUSED && engine != QFS_ENGINE_STAGED)) return QFS_ERR_FORM;
-  if (engine == QFS_ENGINE_STAGED && form != QFS_FORM_DP4A) return QFS_ERR_FORM;
+  const int power = opts && opts->power >= 0 ? opts->power : QFS_POWER_CHAIN;
+  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY) return QFS_ERR_FORM;
+  if (engine == QFS_ENGINE_STAGED && (form != QFS_FORM_DP4A || power != QFS_POWER_CHAIN)) return QFS_ERR_FORM;
   if (n_items == 0) return QFS_OK;
 
   std::lock_guard<std::mutex> lock(g_mu);
@@ -277,6 +286,8 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
     prm.g[k].coeffs = g.coeffs;
     prm.g[k].heights = g.heights_out;
     prm.g[k].item_begin = begin;
+    prm.g[k].tile_round = tile_for(g.p).round_chunks;
+    prm.g[k].tile_ring = tile_for(g.p).ring_words;
     begin += g.n;
     ++k;
   }
@@ -284,10 +295,16 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   prm.n_items = n_items;
   prm.max_h = max_h;
   prm.sw_len = 4 * max_p * (max_p - 1) + 2;
+  prm.power_mode = power;
   if (engine == QFS_ENGINE_STAGED) return run_staged(*S, prm, opts, stream);
 
+  // shared memory: the largest iterate pair of the launch plus the largest ring any group's tile needs
+  int ring_words = 0;
+  for (int i = 0; i < prm.n_groups; ++i)
+    ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p)));
+  const size_t smem = ring_offset_for(tet(4 * (max_p - 1) + 1)) + 4 * (size_t)ring_words;
   Plan plan;
-  rc = make_plan(*S, form, max_p, n_items, opts, plan);
+  rc = make_plan(*S, form, max_p, n_items, opts, plan, smem);
   if (rc) return rc;
   prm.counter = reinterpret_cast<unsigned long long *>(S->ctrl);
   prm.status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
@@ -323,7 +340,7 @@ int qfs_plan_prepare(int p, int64_t n_hint) {
   Plan plan;
   int64_t n = n_hint > 0 ? n_hint : (int64_t)1 << 40;
   for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A, QFS_FORM_INT8TC}) {
-    rc = make_plan(*S, form, p, n, nullptr, plan);
+    rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p)));
     if (rc) return rc;
   }
   cudaError_t e = cudaDeviceSynchronize();
@@ -346,6 +363,85 @@ int qfs_shutdown(void) {
   }
   cudaSetDevice(cur);
   return rc;
+}
+
+int qfs_tune_set(int p, int round_chunks, size_t ring_bytes) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (round_chunks == 0 && ring_bytes == 0) {
+    g_tile[p] = TileConfig{0, 0};
+    return QFS_OK;
+  }
+  const int ring_words = (int)(ring_bytes / 4);
+  if (round_chunks < 32 || round_chunks > 4096 || ring_words < 1024) return QFS_ERR_FORM;
+  const TileConfig t{round_chunks, ring_words};
+  const size_t smem = smem_bytes_for(p, t);
+  if (smem > 227 * 1024) return QFS_ERR_NO_MEMORY;
+  g_tile[p] = t;
+  return QFS_OK;
+}
+
+int qfs_tune_get(int p, int *round_chunks, size_t *ring_bytes, size_t *smem_bytes) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  const TileConfig t = tile_for(p);
+  if (round_chunks) *round_chunks = t.round_chunks;
+  if (ring_bytes) *ring_bytes = 4 * (size_t)t.ring_words;
+  if (smem_bytes) *smem_bytes = smem_bytes_for(p, t);
+  return QFS_OK;
+}
+
+int qfs_autotune(int p, int64_t n, const uint8_t *coeffs, int form, int *best_round, size_t *best_ring,
+                 float *best_ms) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (n <= 0) return QFS_ERR_INVALID_N;
+  if (!coeffs) return QFS_ERR_NULL;
+  if (!form_supported(form)) return QFS_ERR_FORM;
+  int8_t *out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int rounds[] = {256, 512, 768, 1024};
+  const size_t rings_small[] = {48 << 10, 64 << 10, 80 << 10};
+  const size_t rings_large[] = {104 << 10, 140 << 10};
+  const size_t *rings = p <= 7 ? rings_small : rings_large;
+  const int nrings = p <= 7 ? 3 : 2;
+  const TileConfig saved = g_tile[p];
+  float best = 1e30f;
+  TileConfig best_t = tile_for(p);
+  int rc = QFS_OK;
+  qfs_options_t opt;
+  memset(&opt, 0, sizeof(opt));
+  opt.form = form;
+  opt.engine = QFS_ENGINE_FUSED;
+  opt.power = QFS_POWER_CHAIN;
+  qfs_group_t g{p, n, coeffs, out};
+  for (int r : rounds)
+    for (int ri = 0; ri < nrings; ++ri) {
+      if (qfs_tune_set(p, r, rings[ri]) != QFS_OK) continue;
+      rc = qfs_heights_multi_ex(1, &g, 10, &opt, 0);  // warm-up (also grows the workspace)
+      if (rc) break;
+      cudaEventRecord(a, 0);
+      rc = qfs_heights_multi_ex(1, &g, 10, &opt, 0);
+      cudaEventRecord(b, 0);
+      if (rc) break;
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        best_t = g_tile[p];
+      }
+    }
+  g_tile[p] = rc ? saved : best_t;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (rc) return rc;
+  if (best_round) *best_round = best_t.round_chunks;
+  if (best_ring) *best_ring = 4 * (size_t)best_t.ring_words;
+  if (best_ms) *best_ms = best;
+  return QFS_OK;
 }
 
 int qfs_read_stats(uint64_t *survivors, uint64_t *theta_steps) {
@@ -405,6 +501,9 @@ __global__ void unpad_kernel(const uint32_t *__restrict__ padded, int m, const i
 
 extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
                                 int32_t *delta_out, int32_t *iters_out, int8_t *height_out) {
+  const int power = form >> 8;
+  form &= 0xFF;
+  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY) return QFS_ERR_FORM;
   if (!valid_p(p)) return QFS_ERR_INVALID_P;
   if (max_h < 1 || max_h > 10) return QFS_ERR_INVALID_MAX_H;
   if (!coeffs || !height_out) return QFS_ERR_NULL;
@@ -440,7 +539,7 @@ extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int for
   cudaMemcpy(SWg, sw.data(), sizeof(int) * (D + 3), cudaMemcpyHostToDevice);
   DebugPtrs dbg{Gp, Dp, gtmp, itmp};
   uint32_t *status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
-  if ((e = form_debug(form, p, coeffs, max_h, height_out, A, B, status, dbg, 0)) != cudaSuccess) return fail(e);
+  if ((e = form_debug(form, p, coeffs, max_h, height_out, A, B, status, dbg, 0, power)) != cudaSuccess) return fail(e);
   if (G_out) unpad_kernel<<<256, 256>>>(Gp, D, SWg, G_out);
   if (delta_out) unpad_kernel<<<256, 256>>>(Dp, D, SWg, delta_out);
   if (g_out) cudaMemcpy(g_out, gtmp, ld * 4, cudaMemcpyDeviceToDevice);

@@ -43,6 +43,7 @@ struct Smem {
   int powp[kMaxP];        // c^p mod p^2
   int slot_tab[2][kMaxUparDecl + 4];  // ring word offsets of the slices a chain round reads (double buffered)
   uint16_t chunk_tab[32 * 40];        // chain block: flat chunk index -> (column - s0) << 8 | chunk
+  int tile_round, tile_ring;          // chain tile configuration of the current quartic's prime
   int64_t item;
   int flag;
   // followed in dynamic shared memory by two byte arrays of ld entries: g (current iterate) and g_next
@@ -66,44 +67,49 @@ __host__ __device__ constexpr size_t ring_offset_for(int max_ld) {
 // -4..-1) followed by the column's chunks, so output chunk c reads slot chunks c and c+1 (input words 4c-4..4c+3).
 // Outputs past a column's end come out as zero by themselves (their inputs are all padding), so no output needs a
 // bounds check outside the Delta_1 epilogue.
-#ifndef QFS_ROUND_CHUNKS
-#define QFS_ROUND_CHUNKS 512
-#endif
-#ifndef QFS_RING_WORDS_SMALL_P
-#define QFS_RING_WORDS_SMALL_P 16384
-#endif
-constexpr int kRingBudgetSmallP = QFS_RING_WORDS_SMALL_P;   // ring words for p <= 7 (64 KB)
-constexpr int kRingBudgetLargeP = 26624;   // ring words for p >= 11 (104 KB)
+// Tile shape of the chain (per prime; the autotuner may change it at run time):
+//   round_chunks  target (column, chunk) items per round: UPAR = ceil(round_chunks / chunks per slice), at most 8
+//   ring_words    shared-memory words the slot ring may use (UPAR shrinks until 2 UPAR + 4 slots fit)
 constexpr int kMaxUpar = 8;
+constexpr int kDefaultRoundChunks = 512;
+constexpr int kRingBudgetSmallP = 16384;   // default ring words for p <= 7 (64 KB)
+constexpr int kRingBudgetLargeP = 26624;   // default ring words for p >= 11 (104 KB)
+
+struct TileConfig {
+  int round_chunks;
+  int ring_words;
+};
+
+__host__ __device__ inline TileConfig default_tile(int p) {
+  return TileConfig{kDefaultRoundChunks, p <= 7 ? kRingBudgetSmallP : kRingBudgetLargeP};
+}
 
 struct ChainTile {
   int CR, stride, slot_words, upar, nslot;
 };
 
-__host__ __device__ inline ChainTile chain_tile(int s0, int m_out, int budget_words) {
+__host__ __device__ inline ChainTile chain_tile(int s0, int m_out, TileConfig tc) {
   ChainTile T;
   const int s_hi = min(s0 + 31, m_out);
   T.CR = chunks_of(s_hi);
   T.stride = 4 * (T.CR + 1);
   T.slot_words = 36 * T.stride;
   const int per_slice = chunk_prefix(s_hi + 1) - chunk_prefix(s0);
-  int up = (QFS_ROUND_CHUNKS + per_slice - 1) / per_slice;
+  int up = (tc.round_chunks + per_slice - 1) / per_slice;
   up = max(1, min(kMaxUpar, up));
-  while (up > 1 && (2 * up + 4) * T.slot_words > budget_words) --up;
+  while (up > 1 && (2 * up + 4) * T.slot_words > tc.ring_words) --up;
   T.upar = up;
   T.nslot = 2 * up + 4;
   return T;
 }
 
-__host__ __device__ inline int ring_budget(int p) { return p <= 7 ? kRingBudgetSmallP : kRingBudgetLargeP; }
-
-// Shared-memory words the ring needs over every product of the chain for prime p.
-__host__ __device__ inline int chain_slot_words(int p) {
+// Shared-memory words the ring needs over every product of the chain for prime p under tile config tc.
+__host__ __device__ inline int chain_slot_words(int p, TileConfig tc) {
   const int D = 4 * p * (p - 1);
   int best = 0;
   for (int m_out = 8; m_out <= D; m_out += 4)
     for (int s0 = 0; s0 <= m_out; s0 += 32) {
-      const ChainTile T = chain_tile(s0, m_out, ring_budget(p));
+      const ChainTile T = chain_tile(s0, m_out, tc);
       best = max(best, T.nslot * T.slot_words);
     }
   return best;
@@ -111,10 +117,14 @@ __host__ __device__ inline int chain_slot_words(int p) {
 
 __host__ __device__ inline int theta_ring_words_for(int p);
 
-__host__ __device__ inline size_t smem_bytes_for(int p) {
-  const int w = max(chain_slot_words(p), theta_ring_words_for(p));
-  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)w;
+__host__ __device__ inline int ring_words_for(int p, TileConfig tc) {
+  return max(chain_slot_words(p, tc), theta_ring_words_for(p));
 }
+
+__host__ __device__ inline size_t smem_bytes_for(int p, TileConfig tc) {
+  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)ring_words_for(p, tc);
+}
+__host__ __device__ inline size_t smem_bytes_for(int p) { return smem_bytes_for(p, default_tile(p)); }
 
 __device__ __forceinline__ void cp_async16(uint32_t *smem, const uint32_t *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -265,7 +275,7 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
   uint32_t tcb[16];
   if (FORM == 2) tc_b_fragments(sm, tcb);
   for (int s0 = 0; s0 <= m_out; s0 += 32) {
-    const ChainTile T = chain_tile(s0, m_out, ring_budget(P));
+    const ChainTile T = chain_tile(s0, m_out, TileConfig{sm.tile_round, sm.tile_ring});
     const int s_last = min(s0 + 31, m_out);
     const int F0 = chunk_prefix(s0);
     const int ccols = T.CR + 1;  // slot chunks per column
@@ -511,7 +521,7 @@ __host__ __device__ constexpr int theta_ring_words() {
 }
 
 template <int P>
-__device__ __forceinline__ bool theta_step_smem(const uint32_t *__restrict__ delta, const Smem &sm,
+__device__ __noinline__ bool theta_step_smem(const uint32_t *__restrict__ delta, const Smem &sm,
                                                 const uint8_t *__restrict__ g, uint8_t *__restrict__ gn,
                                                 uint32_t *ring) {
   using Pr = Prime<P>;
@@ -627,6 +637,14 @@ __host__ __device__ inline int theta_ring_words_for(int p) {
 
 // ------------------------------------------------------------------------------------------------ one quartic
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code (thread 0 writes it).
+// The same product behind a call boundary, for the cold call sites (the first p-2 products, the identity power
+// mode): inlining the large tiled loop at every call site would multiply the build time without a speed gain.
+template <int P, int FORM, bool DEBUG>
+__device__ __noinline__ void chain_step_call(const uint32_t *in, uint32_t *out, int m_in, Smem &sm, uint32_t *ring,
+                                             const uint8_t *gs, uint32_t *status, DebugPtrs dbg) {
+  chain_step<P, FORM, false, DEBUG>(in, out, m_in, sm, ring, gs, status, dbg);
+}
+
 // A1: read the 35 coefficients into the tap tables; returns false (after a barrier) if one is >= p.
 template <int P>
 __device__ __forceinline__ bool setup_quartic(const uint8_t *__restrict__ f35, Smem &sm) {
@@ -682,7 +700,7 @@ __device__ __forceinline__ uint32_t *power_to_g(Smem &sm, uint8_t *gs, uint32_t 
   uint32_t *cur = bufA, *nxt = bufB;
   int m = 4;
   for (int k = 1; k <= P - 2; ++k) {
-    chain_step<P, FORM, false, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
+    chain_step_call<P, FORM, DEBUG>(cur, nxt, m, sm, ring, gs, status, dbg);
     __syncthreads();
     uint32_t *t = cur; cur = nxt; nxt = t;
     m += 4;
@@ -731,11 +749,158 @@ __device__ __forceinline__ bool theta_any(const uint32_t *delta, Smem &sm, const
   return __syncthreads_or(any ? 1 : 0) != 0;
 }
 
+// ------------------------------------------------------------------------------------------------ identity power
+// A4 + A5 by an exact algebraic shortcut (power mode QFS_POWER_IDENTITY).  It produces the same Delta_1(f^(p-1))
+// array as the chain, and the chain stays the literal reading of Algorithm 1.
+//   Write f~^p = A + p D~ with A = sum_I a~_I^p x^(pI) and D~ = Delta_1(f) mod p (Proposition of Sec. 3.1).  Then
+//   lift(g)^p = f~^(p(p-1)) = (A + p D~)^(p-1) = A^(p-1) - p A^(p-2) D~ (mod p^2), and A = f(x^p) (mod p), so
+//     Delta_1(f^(p-1)) = E(x^p) - f^(p-2)(x^p) Delta_1(f)   (mod p),
+//   E_J = (A~^(p-1)[J] - c~_J^p) / p with A~(y) = sum_I (a~_I^p mod p^2) y^I and c_J the coefficients of g.
+// Work per quartic at p = 7: one chain product to f~^p, p-2 small products for A~^(p-1), and about 8e6 MACs for
+// f^(p-2)(x^p) Delta_1(f) -- against 2.9e8 for the chain.
+template <int P, int FORM, bool DEBUG>
+__device__ __noinline__ uint32_t *power_identity(Smem &sm, const uint8_t *gs, uint32_t *ring, uint32_t *cur,
+                                                    uint32_t *other, uint32_t *status, DebugPtrs dbg) {
+  using Pr = Prime<P>;
+  constexpr int d = Pr::d, D = Pr::D, dm = 4 * (P - 2), d1 = 4 * P;
+  constexpr int l_fpm2 = tet(dm + 1), l_d1f = tet(d1 + 1), l_E = Pr::ld;
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  // byte scratch in global memory after f~^p in `other`
+  uint8_t *fpm2_g = reinterpret_cast<uint8_t *>(other + sm.SW[d1 + 1]);
+  uint8_t *d1f_g = fpm2_g + l_fpm2;
+  uint8_t *E_g = d1f_g + l_d1f;
+  // f^(p-2) mod p: `other` holds f~^(p-2) (degree dm) after power_to_g
+  for (int k = tid; k < sm.SW[dm + 1] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, dm, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(other + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16 && 16 * c + b <= s; ++b)
+      fpm2_g[tet(u) + tri(s) + 16 * c + b] = (uint8_t)(((w[b >> 2] >> (8 * (b & 3))) & 0xFFu) % P);
+  }
+  __syncthreads();
+  // f~^p = f~^(p-1) f~ (mod p^2) into `other`, then Delta_1(f) = (f~^p - sum a~_I^p x^(pI)) / p mod p
+  chain_step_call<P, FORM, DEBUG>(cur, other, d, sm, ring, gs, status, dbg);
+  __syncthreads();
+  bool bad = false;
+  for (int k = tid; k < sm.SW[d1 + 1] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, d1, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(other + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16 && 16 * c + b <= s; ++b) {
+      const int t = 16 * c + b;
+      int G = (int)((w[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+      if ((u % P) == 0 && (s % P) == 0 && (t % P) == 0) {
+        G -= sm.powp[sm.taps[tet(u / P) + tri(s / P) + t / P]];
+        if (G < 0) G += Pr::p2;
+      }
+      if (G % P) bad = true;
+      d1f_g[tet(u) + tri(s) + t] = (uint8_t)(G / P);
+    }
+  }
+  __syncthreads();
+  // A~ (coefficients a~_I^p mod p^2) into cur, then A~^(p-1) mod p^2 by p-2 chain products (ping-pong inside cur)
+  if (tid < 35) sm.taps[tid] = sm.powp[sm.taps[tid]];
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t mask = 0;
+    for (int uI = 0; uI <= 4; ++uI)
+      for (int sI = 0; sI <= uI; ++sI) {
+        uint32_t tw = 0;
+        bool nz = false;
+        for (int tI = 0; tI <= sI; ++tI) {
+          const int a = sm.taps[tet(uI) + tri(sI) + tI];
+          nz |= a != 0;
+          if (tI <= 3) tw |= (uint32_t)a << (8 * (3 - tI));
+        }
+        sm.tapword[tri(uI) + sI] = tw;
+        if (nz) mask |= 1u << (tri(uI) + sI);
+      }
+    sm.pair_mask = mask;
+  }
+  uint32_t *pa = cur, *pb = cur + sm.SW[d + 1];
+  for (int k = tid; k < sm.SW[5] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, 4, sm.SW, u, s, c);
+    uint32_t words[4] = {0, 0, 0, 0};
+    for (int t = 0; t <= s; ++t) words[t >> 2] |= (uint32_t)sm.taps[tet(u) + tri(s) + t] << (8 * (t & 3));
+    *reinterpret_cast<uint4 *>(pa + 4 * k) = make_uint4(words[0], words[1], words[2], words[3]);
+  }
+  __syncthreads();
+  for (int m = 4; m < d; m += 4) {
+    chain_step_call<P, FORM, DEBUG>(pa, pb, m, sm, ring, gs, status, dbg);
+    __syncthreads();
+    uint32_t *t = pa; pa = pb; pb = t;
+  }
+  // E_J = (A~^(p-1)[J] - c~_J^p) / p mod p
+  for (int k = tid; k < sm.SW[d + 1] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, d, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(pa + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16 && 16 * c + b <= s; ++b) {
+      const int J = tet(u) + tri(s) + 16 * c + b;
+      int G = (int)((w[b >> 2] >> (8 * (b & 3))) & 0xFFu) - sm.powp[gs[J]];
+      if (G < 0) G += Pr::p2;
+      if (G % P) bad = true;
+      E_g[J] = (uint8_t)(G / P);
+    }
+  }
+  __syncthreads();
+  // stage the three small arrays in shared memory
+  uint8_t *fpm2 = reinterpret_cast<uint8_t *>(ring), *d1f = fpm2 + l_fpm2, *E = d1f + l_d1f;
+  for (int i = tid; i < l_fpm2 + l_d1f + l_E; i += nthreads) fpm2[i] = fpm2_g[i];
+  __syncthreads();
+  // Delta[e] = E(x^p)[e] - sum_{pJ + K = e} f^(p-2)[J] Delta_1(f)[K] mod p, written to cur in the padded layout
+  uint32_t *delta = cur;
+  for (int k = tid; k < sm.SW[D + 1] / 4; k += nthreads) {
+    int ue, se, c;
+    decode_form_chunk(k, D, sm.SW, ue, se, c);
+    int acc[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) acc[b] = 0;
+    const int uj_lo = ue > d1 ? (ue - d1 + P - 1) / P : 0, uj_hi = min(dm, ue / P);
+    for (int uj = uj_lo; uj <= uj_hi; ++uj) {
+      const int uk = ue - P * uj;
+      const int sj_lo = se > uk ? (se - uk + P - 1) / P : 0, sj_hi = min(uj, se / P);
+      for (int sj = sj_lo; sj <= sj_hi; ++sj) {
+        const int sk = se - P * sj;
+        const uint8_t *fj = fpm2 + tet(uj) + tri(sj);
+        const uint8_t *dk = d1f + tet(uk) + tri(sk);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const int te = 16 * c + b;
+          if (te <= se) {
+            const int tj_lo = te > sk ? (te - sk + P - 1) / P : 0, tj_hi = min(sj, te / P);
+            for (int tj = tj_lo; tj <= tj_hi; ++tj) acc[b] += (int)fj[tj] * (int)dk[te - P * tj];
+          }
+        }
+      }
+    }
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const int te = 16 * c + b;
+      if (te <= se) {
+        int v = -(acc[b] % P);
+        if ((ue % P) == 0 && (se % P) == 0 && (te % P) == 0) v += E[tet(ue / P) + tri(se / P) + te / P];
+        if (v < 0) v += P;
+        w[b >> 2] |= (uint32_t)v << (8 * (b & 3));
+      }
+    }
+    *reinterpret_cast<uint4 *>(delta + 4 * k) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  if (bad) atomicOr(status, kStatusInexactDivision);
+  __syncthreads();
+  return delta;
+}
+
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code.
 template <int P, int FORM, bool DEBUG>
 __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
                                uint32_t *ring, uint32_t *bufA, uint32_t *bufB, uint32_t *status, DebugPtrs dbg,
-                               int &theta_steps) {
+                               int &theta_steps, int power_mode = 0) {
   using Pr = Prime<P>;
   const int tid = threadIdx.x;
   theta_steps = 0;
@@ -747,8 +912,13 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   if (gs[Pr::witness] != 0) return 1;
   // A4 + A5 into `other` or `cur`, whichever the chain's parity leaves last
   constexpr int nsteps = P * (P - 1) - (P - 1);   // products from f~^(p-1) to f~^(p(p-1))
-  uint32_t *delta = (nsteps % 2) ? other : cur;
-  power_to_G<P, FORM, true, DEBUG>(sm, gs, ring, cur, other, nullptr, status, dbg);
+  uint32_t *delta;
+  if (power_mode == 1) {
+    delta = power_identity<P, FORM, DEBUG>(sm, gs, ring, cur, other, status, dbg);
+  } else {
+    delta = (nsteps % 2) ? other : cur;
+    power_to_G<P, FORM, true, DEBUG>(sm, gs, ring, cur, other, nullptr, status, dbg);
+  }
   if (DEBUG)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
   // A6 + A7
@@ -773,6 +943,7 @@ struct FusedGroup {
   const uint8_t *coeffs;
   int8_t *heights;
   int64_t item_begin;
+  int tile_round, tile_ring;
 };
 
 constexpr int kMaxGroups = 8;
@@ -788,6 +959,7 @@ struct FusedParams {
   unsigned long long *stats;          // [0] quartics past the height-1 test, [1] theta steps run
   uint32_t *ws;                       // 2 buffers of ws_words per CTA
   size_t ws_words;
+  int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut
 };
 
 template <int FORM>
@@ -814,14 +986,18 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
     while (gi + 1 < prm.n_groups && item >= prm.g[gi + 1].item_begin) ++gi;
     const FusedGroup &G = prm.g[gi];
     const int64_t row = item - G.item_begin;
+    if (threadIdx.x == 0) {
+      sm.tile_round = G.tile_round;
+      sm.tile_ring = G.tile_ring;
+    }
     const uint8_t *f = G.coeffs + 35 * row;
     int h, steps;
     switch (G.p) {
-      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
-      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
-      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
-      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
-      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps); break;
+      case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+      case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
     }
     if (threadIdx.x == 0) {
       G.heights[row] = (int8_t)h;

@@ -17,16 +17,21 @@ __global__ void __launch_bounds__(kThreads, QFS_MIN_CTAS_PER_SM) fused_kernel(Fu
 // One quartic with every intermediate array written out (kernel-level parity hook).
 template <int P, int FORM>
 __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,
-                                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg) {
+                                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg,
+                                                         int power_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   uint8_t *gs = smem_raw + sizeof(Smem);
   uint8_t *gn = gs + Prime<P>::ld;
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(Prime<P>::ld));
   build_sw(sm.SW, Prime<P>::D + 2);
+  if (threadIdx.x == 0) {
+    sm.tile_round = default_tile(P).round_chunks;
+    sm.tile_ring = default_tile(P).ring_words;
+  }
   __syncthreads();
   int steps = 0;
-  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, ring, bufA, bufB, status, dbg, steps);
+  const int h = process_quartic<P, FORM, true>(f, max_h, sm, gs, gn, ring, bufA, bufB, status, dbg, steps, power_mode);
   if (threadIdx.x == 0) *h_out = (int8_t)h;
 }
 
@@ -36,12 +41,12 @@ struct FormLauncher {
   static cudaError_t fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st);
   static cudaError_t occupancy(int *blocks_per_sm, size_t smem);
   static cudaError_t debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA, uint32_t *bufB,
-                           uint32_t *status, DebugPtrs dbg, cudaStream_t st);
+                           uint32_t *status, DebugPtrs dbg, cudaStream_t st, int power_mode);
 };
 
 #define QFS_DEBUG_LAUNCH(PP, FORM)                                                                            \
   e = cudaFuncSetAttribute(debug_kernel<PP, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-  if (e == cudaSuccess) debug_kernel<PP, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg)
+  if (e == cudaSuccess) debug_kernel<PP, FORM><<<1, kThreads, smem, st>>>(f, max_h, h_out, bufA, bufB, status, dbg, power_mode)
 
 #define QFS_DEFINE_FORM_LAUNCHER(FORM)                                                                        \
   template <>                                                                                                 \
@@ -63,7 +68,8 @@ struct FormLauncher {
 #define QFS_DEFINE_DEBUG_LAUNCHER(FORM)                                                                       \
   template <>                                                                                                 \
   cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
-                                        uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st) {   \
+                                        uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st,     \
+                                        int power_mode) {                                                     \
     const size_t smem = smem_bytes_for(p);                                                                    \
     cudaError_t e = cudaSuccess;                                                                              \
     switch (p) {                                                                                              \

@@ -99,6 +99,8 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   prm.g[0].coeffs = coeffs;
   prm.g[0].heights = heights_out;
   prm.g[0].item_begin = 0;
+  prm.g[0].tile_round = default_tile(p).round_chunks;
+  prm.g[0].tile_ring = default_tile(p).ring_words;
   prm.n_groups = 1;
   prm.n_items = n;
   prm.max_h = max_h;
@@ -108,6 +110,7 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   prm.stats = reinterpret_cast<unsigned long long *>(base + 16);
   prm.ws = reinterpret_cast<uint32_t *>(base + kControlBytes);
   prm.ws_words = ws_words;
+  prm.power_mode = QFS_POWER_CHAIN;
   // The array keeps whatever the previous call left; only the control block must start at zero.  The chain
   // buffers need no clearing: every word a CTA reads is written earlier in the same quartic.
   e = cudaMemsetAsync(base, 0, kControlBytes, stream);

@@ -47,6 +47,10 @@ template <int P>
 __device__ __forceinline__ void stage_smem(Smem *&sm, uint8_t *&gs, uint8_t *&gn, uint32_t *&ring) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   sm = reinterpret_cast<Smem *>(smem_raw);
+  if (threadIdx.x == 0) {
+    sm->tile_round = default_tile(P).round_chunks;
+    sm->tile_ring = default_tile(P).ring_words;
+  }
   gs = smem_raw + sizeof(Smem);
   gn = gs + Prime<P>::ld;
   ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(Prime<P>::ld));

@@ -16,6 +16,8 @@ FORM_INT32, FORM_DP4A, FORM_INT8TC = 0, 1, 2
 ENGINE_FUSED, ENGINE_STAGED = 0, 1
 FORMS = {"int32": FORM_INT32, "dp4a": FORM_DP4A, "int8tc": FORM_INT8TC}
 ENGINES = {"fused": ENGINE_FUSED, "staged": ENGINE_STAGED}
+POWER_CHAIN, POWER_IDENTITY = 0, 1
+POWERS = {"chain": POWER_CHAIN, "identity": POWER_IDENTITY}
 MAX_GROUPS = 8
 PRIMES = (3, 5, 7, 11, 13)
 
@@ -36,7 +38,7 @@ class Group(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("engine", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("max_ctas", ctypes.c_int), ("workspace_budget", ctypes.c_size_t)]
+                ("max_ctas", ctypes.c_int), ("workspace_budget", ctypes.c_size_t), ("power", ctypes.c_int)]
 
 
 _LIB = None
@@ -62,11 +64,17 @@ def _lib():
         L.qfs_last_cuda_error.argtypes = []
         L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
         L.qfs_heights_noalloc.argtypes = [c_int, i64, vp, c_int, vp, vp]
+        L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
+        L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_size_t)]
+        L.qfs_autotune.argtypes = [c_int, i64, vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_float)]
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
-                     "qfs_debug_stages", "qfs_heights_noalloc"):
+                     "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune"):
             getattr(L, name).restype = c_int
         _LIB = L
+        load_tile_table()
     return _LIB
 
 
@@ -95,8 +103,9 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _options(form, engine, ctas_per_sm, max_ctas, workspace_budget):
+def _options(form, engine, ctas_per_sm, max_ctas, workspace_budget, power=None):
     o = Options()
+    o.power = POWERS[power] if isinstance(power, str) else (-1 if power is None else int(power))
     o.form = FORMS[form] if isinstance(form, str) else (-1 if form is None else int(form))
     o.engine = ENGINES[engine] if isinstance(engine, str) else (-1 if engine is None else int(engine))
     o.ctas_per_sm = int(ctas_per_sm)
@@ -106,7 +115,7 @@ def _options(form, engine, ctas_per_sm, max_ctas, workspace_budget):
 
 
 def heights(p, coeffs, max_h=10, out=None, stream=None, form=None, engine=None, ctas_per_sm=0, max_ctas=0,
-            workspace_budget=0):
+            workspace_budget=0, power=None):
     """Heights of the quartics in `coeffs` (CUDA uint8 tensor, n x 35, descending lex) over F_p.
 
     Returns an int8 CUDA tensor of n codes (1..max_h height, 0 infinity, -1 invalid row).  Asynchronous on the
@@ -120,11 +129,11 @@ def heights(p, coeffs, max_h=10, out=None, stream=None, form=None, engine=None, 
         out = torch.empty(n, dtype=torch.int8, device=coeffs.device)
     _need_cuda(out, torch.int8, "out")
     return heights_multi([(p, coeffs, out)], max_h, stream, form, engine, ctas_per_sm, max_ctas,
-                         workspace_budget)[0]
+                         workspace_budget, power)[0]
 
 
 def heights_multi(groups, max_h=10, stream=None, form=None, engine=None, ctas_per_sm=0, max_ctas=0,
-                  workspace_budget=0):
+                  workspace_budget=0, power=None):
     """One launch over several (p, coeffs, out) batches; `out` may be None.  Returns the list of outputs."""
     if not 1 <= len(groups) <= MAX_GROUPS:
         raise ValueError(f"between 1 and {MAX_GROUPS} groups")
@@ -142,7 +151,7 @@ def heights_multi(groups, max_h=10, stream=None, form=None, engine=None, ctas_pe
         arr[i].p, arr[i].n = int(p), int(coeffs.shape[0])
         arr[i].coeffs, arr[i].heights_out = coeffs.data_ptr(), out.data_ptr()
         outs.append(out)
-    opts = _options(form, engine, ctas_per_sm, max_ctas, workspace_budget)
+    opts = _options(form, engine, ctas_per_sm, max_ctas, workspace_budget, power)
     rc = _lib().qfs_heights_multi_ex(len(groups), arr, int(max_h), ctypes.byref(opts), _stream(stream))
     _check(rc, "qfs_heights_multi_ex")
     return outs
@@ -163,6 +172,49 @@ def heights_noalloc(p, coeffs, max_h=10, out=None, stream=None):
                                     _stream(stream))
     _check(rc, "qfs_heights_noalloc")
     return out
+
+
+TILE_TABLE = os.path.join(_HERE, "tile_table.json")
+
+
+def tune_set(p, round_chunks, ring_bytes):
+    _check(_lib().qfs_tune_set(int(p), int(round_chunks), int(ring_bytes)), "qfs_tune_set")
+
+
+def tune_get(p):
+    r, ring, smem = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(_lib().qfs_tune_get(int(p), ctypes.byref(r), ctypes.byref(ring), ctypes.byref(smem)), "qfs_tune_get")
+    return dict(round_chunks=r.value, ring_bytes=ring.value, smem_bytes=smem.value)
+
+
+def autotune(p, sample, form="dp4a"):
+    """Times every candidate chain tile shape on `sample` (CUDA uint8 n x 35) and keeps the fastest for p."""
+    _need_cuda(sample, torch.uint8, "sample")
+    r, ring, ms = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_float(0)
+    rc = _lib().qfs_autotune(int(p), int(sample.shape[0]), sample.data_ptr(),
+                             FORMS[form] if isinstance(form, str) else int(form), ctypes.byref(r), ctypes.byref(ring),
+                             ctypes.byref(ms))
+    _check(rc, "qfs_autotune")
+    return dict(p=int(p), round_chunks=r.value, ring_bytes=ring.value, ms=ms.value)
+
+
+def save_tile_table(entries, path=TILE_TABLE):
+    """Persists autotuner results ({p: {round_chunks, ring_bytes, ...}}) as JSON."""
+    import json
+    with open(path, "w") as fh:
+        json.dump({str(k): v for k, v in entries.items()}, fh, indent=1, sort_keys=True)
+
+
+def load_tile_table(path=TILE_TABLE):
+    """Applies a persisted tile table (missing file: nothing to do).  Returns the entries applied."""
+    import json
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        table = json.load(fh)
+    for p, v in table.items():
+        tune_set(int(p), v["round_chunks"], v["ring_bytes"])
+    return table
 
 
 def set_default_form(form):
@@ -190,7 +242,7 @@ def read_stats():
     return a.value, b.value
 
 
-def debug_stages(p, coeffs, max_h=10, form="dp4a"):
+def debug_stages(p, coeffs, max_h=10, form="dp4a", power="chain"):
     """Runs the device pipeline on one quartic and returns every intermediate array (int32 CUDA tensors,
     descending lex): dict(h, g, G, delta, iters).  Synchronous; for parity tests."""
     _need_cuda(coeffs, torch.uint8, "coeffs")
@@ -205,8 +257,8 @@ def debug_stages(p, coeffs, max_h=10, form="dp4a"):
     iters = torch.zeros(max(max_h - 1, 1), ld, dtype=torch.int32, device=dev)
     h = torch.zeros(1, dtype=torch.int8, device=dev)
     torch.cuda.synchronize(dev)
-    rc = _lib().qfs_debug_stages(int(p), coeffs.data_ptr(), int(max_h), FORMS[form] if isinstance(form, str)
-                                 else int(form), g.data_ptr(), G.data_ptr(), delta.data_ptr(), iters.data_ptr(),
-                                 h.data_ptr())
+    fcode = (FORMS[form] if isinstance(form, str) else int(form)) | (POWERS[power] << 8)
+    rc = _lib().qfs_debug_stages(int(p), coeffs.data_ptr(), int(max_h), fcode, g.data_ptr(), G.data_ptr(),
+                                 delta.data_ptr(), iters.data_ptr(), h.data_ptr())
     _check(rc, "qfs_debug_stages")
     return dict(h=int(h.item()), g=g, G=G, delta=delta, iters=iters)

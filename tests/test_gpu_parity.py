@@ -253,3 +253,83 @@ def test_staged_engine_small_chunks_and_multi(qfs):
     outs = qfs.heights_multi([(5, t5, None), (7, t7, None)], engine="staged", workspace_budget=64 << 20)
     assert np.array_equal(outs[0].cpu().numpy(), oracle.heights(5, f5))
     assert np.array_equal(outs[1].cpu().numpy(), oracle.heights(7, f7))
+
+
+# ------------------------------------------------------------------------------------- identity power mode
+@pytest.mark.parametrize("p,n", [(3, 6), (5, 6)])
+def test_identity_power_stage_arrays(qfs, p, n):
+    # the identity mode forms the same Delta_1(f^(p-1)) array as Algorithm 1, element by element
+    f, h = find_rows(p, 400, 700 + p, lambda x: x >= 2 or x == 0, n)
+    for row in f:
+        ref = oracle.stage_arrays_a(p, row)
+        for form in CORE_FORMS:
+            got = qfs.debug_stages(p, dev_tensor(row), form=form, power="identity")
+            assert got["h"] == ref["h"]
+            assert np.array_equal(got["delta"].cpu().numpy(), ref["delta"]), form
+            rows = ref["iters"].shape[0]
+            assert np.array_equal(got["iters"].cpu().numpy()[:rows], ref["iters"]), form
+
+
+@pytest.mark.parametrize("p,n", [(3, 1500), (5, 3000), (7, 800), (11, 24), (13, 6)])
+def test_identity_power_heights(qfs, p, n):
+    f = np.concatenate([inputs.dense(p, n, 7500 + p), inputs.sparse(p, n, 7600 + p)])
+    t = dev_tensor(f)
+    want = oracle.heights(p, f)
+    for form in CORE_FORMS:
+        assert np.array_equal(qfs.heights(p, t, form=form, power="identity").cpu().numpy(), want), form
+    assert qfs.read_status() == 0
+
+
+def test_identity_power_paper_examples(qfs):
+    for p in (5, 7, 11, 13):
+        sel = [r for r in example_quartics() if r[0] == p]
+        f = np.stack([r[3] for r in sel])
+        want = np.array([r[1] for r in sel], np.int8)
+        assert np.array_equal(qfs.heights(p, dev_tensor(f), power="identity").cpu().numpy(), want), p
+
+
+# ------------------------------------------------------------------------------------- tile autotuner, graphs
+def test_tile_shapes_do_not_change_heights(qfs):
+    p = 7
+    f = inputs.dense(p, 1200, 6600)
+    t = dev_tensor(f)
+    want = oracle.heights(p, f)
+    saved = qfs.tune_get(p)
+    try:
+        for rc, ring in [(256, 48 << 10), (1024, 80 << 10), (64, 32 << 10)]:
+            qfs.tune_set(p, rc, ring)
+            assert qfs.tune_get(p)["round_chunks"] == rc
+            assert np.array_equal(qfs.heights(p, t).cpu().numpy(), want)
+        with pytest.raises(qfs.QfsError):
+            qfs.tune_set(p, 8, 48 << 10)
+        best = qfs.autotune(p, t[:400])
+        assert best["round_chunks"] >= 32 and best["ms"] > 0
+        assert np.array_equal(qfs.heights(p, t).cpu().numpy(), want)
+    finally:
+        qfs.tune_set(p, saved["round_chunks"], saved["ring_bytes"])
+
+
+def test_cuda_graph_capture_and_replay(qfs):
+    # the call is stream-ordered and allocation-free once the workspace exists, so it can be captured
+    p = 5
+    a = inputs.dense(p, 3000, 6700)
+    want = oracle.heights(p, a)
+    coeffs = dev_tensor(a)
+    out = torch.empty(3000, dtype=torch.int8, device="cuda:0")
+    qfs.heights(p, coeffs, out=out)              # sizes the workspace before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g):
+        qfs.heights(p, coeffs, out=out)
+    for _ in range(2):
+        out.fill_(-5)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want)
+    # new inputs in the same buffer replay through the same graph
+    b = inputs.sparse(p, 3000, 6701)
+    coeffs.copy_(torch.from_numpy(b))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.heights(p, b))
