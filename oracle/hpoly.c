@@ -82,12 +82,20 @@ int hpoly_mul_mod(hpoly *C, const hpoly *A, const hpoly *B, int64_t m) {
       }
   free(boff);
   free(bval);
+#if QFS_MUTATE != 9 /* planted mistake 9: products left unreduced */
   hpoly_reduce(C, m);
+#endif
   return 0;
 }
 
 void hpoly_from_desc_lex(hpoly *P, const int64_t *coeffs) {
   int64_t k = 0;
+#if QFS_MUTATE == 10 /* planted mistake: coefficients read in ascending instead of descending lex order */
+  for (int e1 = 0; e1 <= P->deg; e1++)
+    for (int e2 = 0; e1 + e2 <= P->deg; e2++)
+      for (int e3 = 0; e1 + e2 + e3 <= P->deg; e3++) *hpoly_at(P, e1, e2, e3) = coeffs[k++];
+  return;
+#endif
   for (int e1 = P->deg; e1 >= 0; e1--)
     for (int e2 = P->deg - e1; e2 >= 0; e2--)
       for (int e3 = P->deg - e1 - e2; e3 >= 0; e3--) *hpoly_at(P, e1, e2, e3) = coeffs[k++];

@@ -12,6 +12,10 @@
  */
 #ifndef QFS_ORACLE_HPOLY_H
 #define QFS_ORACLE_HPOLY_H
+/* QFS_MUTATE = k compiles planted mistake k (tests check that the pins catch each one); 0 = the oracle. */
+#ifndef QFS_MUTATE
+#define QFS_MUTATE 0
+#endif
 #include <stdint.h>
 
 typedef struct {

@@ -20,31 +20,41 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
 _lib = None
 
-__all__ = ["build", "lib", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
+__all__ = ["build", "lib", "load", "Oracle", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
            "stage_arrays_a", "stage_arrays_r", "ROUTE_A", "ROUTE_R"]
 
 ROUTE_A = 0
 ROUTE_R = 1
 
 
-def build(force=False):
-    """Compile the oracle with gcc (portable C11, no architecture flags) and return the library path."""
+def build(force=False, defines=(), path=None):
+    """Compile the oracle with gcc (portable C11, no architecture flags) and return the library path.
+
+    `defines` (e.g. ["QFS_MUTATE=3"]) and `path` build a variant elsewhere; tests use that to plant mistakes."""
     os.makedirs(_BUILD, exist_ok=True)
+    out = path or _LIB_PATH
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "hpoly.h")])
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lpthread"]
+    if force or defines or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = (["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-o", tmp] + [f"-D{d}" for d in defines]
+               + srcs + ["-lpthread"])
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, out)
+    return out
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB_PATH)
+        _lib = load(build())
+    return _lib
+
+
+def load(path):
+    """ctypes handle of an oracle library build (argument types set)."""
+    if True:
+        L = ctypes.CDLL(path)
         i32p = ctypes.POINTER(ctypes.c_int32)
         u8p = ctypes.POINTER(ctypes.c_uint8)
         L.qfs_oracle_height_a.argtypes = [ctypes.c_int, u8p, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p]
@@ -58,8 +68,27 @@ def lib():
         L.qfs_oracle_delta1.restype = ctypes.c_int
         L.qfs_oracle_split_u.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p]
         L.qfs_oracle_split_u.restype = ctypes.c_int
-        _lib = L
-    return _lib
+    return L
+
+
+class Oracle:
+    """The oracle's Python API bound to one library build (the module functions use the default build)."""
+
+    def __init__(self, L):
+        self._L = L
+
+    def __getattr__(self, name):
+        fn = globals()[name]
+
+        def bound(*a, **k):
+            global _lib
+            saved = _lib
+            _lib = self._L
+            try:
+                return fn(*a, **k)
+            finally:
+                _lib = saved
+        return bound
 
 
 def monomial_count(d):

@@ -44,7 +44,11 @@ static int delta1_alg1(int p, const hpoly *g, int lift_signed, hpoly *D_out, hpo
   memcpy(D.c, lift.c, n * sizeof(int64_t));
   hpoly_reduce(&D, p2);
   for (int k = 2; k <= p; k++) {
+#if QFS_MUTATE == 4 /* planted mistake: lift^p taken mod p instead of mod p^2 */
+    if (hpoly_mul_mod(&next, &D, &lift, p)) { hpoly_free(&D); hpoly_free(&lift); return -1; }
+#else
     if (hpoly_mul_mod(&next, &D, &lift, p2)) { hpoly_free(&D); hpoly_free(&lift); return -1; }
+#endif
     hpoly_free(&D);
     D = next;
   }
@@ -58,8 +62,16 @@ static int delta1_alg1(int p, const hpoly *g, int lift_signed, hpoly *D_out, hpo
       for (int e3 = 0; e1 + e2 + e3 <= g->deg; e3++) {
         int64_t c = *hpoly_at(&lift, e1, e2, e3);
         if (c == 0) continue;
+#if QFS_MUTATE == 14 /* planted mistake: t^p subtracted at a transposed lattice point */
+        int64_t *slot = hpoly_at(&D, p * e2, p * e1, p * e3);
+#else
         int64_t *slot = hpoly_at(&D, p * e1, p * e2, p * e3);
+#endif
+#if QFS_MUTATE == 8 /* planted mistake: c^(p-1) subtracted instead of c^p */
+        *slot = mod_pos(*slot - ipow_mod(c, p - 1, p2), p2);
+#else
         *slot = mod_pos(*slot - ipow_mod(c, p, p2), p2);
+#endif
       }
   hpoly_free(&lift);
   /* D <- D / p: exact division, then the result is read mod p. */
@@ -68,7 +80,11 @@ static int delta1_alg1(int p, const hpoly *g, int lift_signed, hpoly *D_out, hpo
   int bad = 0;
   for (size_t i = 0; i < nd; i++) {
     if (D.c[i] % p != 0) bad = 1;
+#if QFS_MUTATE == 1 /* planted mistake: sign of Delta_1 */
+    Delta->c[i] = mod_pos(-(D.c[i] / p), p);
+#else
     Delta->c[i] = mod_pos(D.c[i] / p, p);
+#endif
   }
   hpoly_free(&D);
   return bad ? -2 : 0;
@@ -87,13 +103,21 @@ static int split_u_alg2(int p, const hpoly *P, hpoly *out) {
         int64_t c = *hpoly_at(P, e1, e2, e3);
         if (c == 0) continue;
         if (e1 % p == p - 1 && e2 % p == p - 1 && e3 % p == p - 1 && e4 % p == p - 1)
+#if QFS_MUTATE == 2 /* planted mistake: transposed output exponents in u */
+          *hpoly_at(out, (e2 - (p - 1)) / p, (e1 - (p - 1)) / p, (e3 - (p - 1)) / p) += c;
+#else
           *hpoly_at(out, (e1 - (p - 1)) / p, (e2 - (p - 1)) / p, (e3 - (p - 1)) / p) += c;
+#endif
       }
   return 0;
 }
 
 static int64_t witness_coeff(int p, const hpoly *g) {
+#if QFS_MUTATE == 3 /* planted mistake: wrong witness monomial */
+  return *hpoly_at(g, p - 1, p - 1, p - 2);
+#else
   return *hpoly_at(g, p - 1, p - 1, p - 1);
+#endif
 }
 
 static int load_quartic(int p, const uint8_t *f35, hpoly *f) {
@@ -157,7 +181,11 @@ int qfs_oracle_height_a(int p, const uint8_t *f35, int max_h, int lift_signed, i
   /* g <- f^(p-1) over F_p */
   if (hpoly_init(&g, 0)) { hpoly_free(&f); return -3; }
   g.c[0] = 1;
+#if QFS_MUTATE == 7 /* planted mistake: f^(p-2) instead of f^(p-1) */
+  for (int k = 1; k <= p - 2; k++) {
+#else
   for (int k = 1; k <= p - 1; k++) {
+#endif
     if (hpoly_mul_mod(&t, &g, &f, p)) { hpoly_free(&g); hpoly_free(&f); return -3; }
     hpoly_free(&g);
     g = t;
@@ -177,7 +205,11 @@ int qfs_oracle_height_a(int p, const uint8_t *f35, int max_h, int lift_signed, i
   if (delta_out) hpoly_to_desc_lex(&Delta, delta_out);
   const int64_t ld = monomial_count(4 * (p - 1));
   int result = 0;
+#if QFS_MUTATE == 12 /* planted mistake: the bound b tested with < instead of <= */
+  for (int h = 2; h < max_h; h++) {
+#else
   for (int h = 2; h <= max_h; h++) {
+#endif
     hpoly prod, next;
     if (hpoly_mul_mod(&prod, &Delta, &g, p)) { result = -3; break; }
     rc = split_u_alg2(p, &prod, &next);
@@ -188,7 +220,11 @@ int qfs_oracle_height_a(int p, const uint8_t *f35, int max_h, int lift_signed, i
     g = next;
     if (iters_out) hpoly_to_desc_lex(&g, iters_out + (int64_t)(h - 2) * ld);
     if (witness_coeff(p, &g) != 0) { result = h; break; }
+#if QFS_MUTATE == 11 /* planted mistake: a zero iterate read as height 1 */
+    if (hpoly_is_zero(&g)) { result = 1; break; }
+#else
     if (hpoly_is_zero(&g)) { result = 0; break; }
+#endif
   }
   hpoly_free(&g);
   hpoly_free(&Delta);

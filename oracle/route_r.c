@@ -102,7 +102,11 @@ int qfs_oracle_height_r(int p, const uint8_t *f35, int max_h, int32_t *d1f_out, 
     if (hpoly_mul_mod(&next, &fpm2, &q, p)) { hpoly_free(&q); result = -3; break; }
     hpoly_free(&q);
     size_t nn = (size_t)next.side * next.side * next.side;
+#if QFS_MUTATE == 6 /* planted mistake: the minus sign of the reduced step dropped */
+    for (size_t i = 0; i < nn; i++) next.c[i] = mod_pos(next.c[i], p);
+#else
     for (size_t i = 0; i < nn; i++) next.c[i] = mod_pos(-next.c[i], p);
+#endif
     hpoly_free(&g);
     g = next;
     if (iters_out) hpoly_to_desc_lex(&g, iters_out + (int64_t)(h - 2) * ld);
