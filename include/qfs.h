@@ -69,8 +69,11 @@ enum {
 /* How A4 + A5 form Delta_1(f^(p-1)) (both produce the same array, bit for bit). */
 enum {
   QFS_POWER_CHAIN = 0,     /* Algorithm 1 literally: lift(g)^p mod p^2 as the chain f~^(p(p-1)), then (G - S) / p */
-  QFS_POWER_IDENTITY = 1   /* the exact rewriting Delta_1(f^(p-1)) = E(x^p) - f^(p-2)(x^p) Delta_1(f) mod p, from
+  QFS_POWER_IDENTITY = 1,  /* the exact rewriting Delta_1(f^(p-1)) = E(x^p) - f^(p-2)(x^p) Delta_1(f) mod p, from
                               f~^p = A + p Delta_1(f) (Proposition of Sec. 3.1) and the binomial theorem mod p^2 */
+  QFS_POWER_REDUCED = 2    /* never forms Delta_1(f^(p-1)): the loop applies theta only to iterates F with a zero
+                              witness coefficient, and for those theta(F) = -f^(p-2) u(F Delta_1(f)) mod p (u moves
+                              x^(pJ) out as x^J, Algorithm 2).  Same heights; about 30x less work per theta step */
 };
 
 #define QFS_MAX_GROUPS 8
@@ -168,7 +171,8 @@ int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int max_h, int8
      delta_out C(4p(p-1)+3,3) values: Delta_1(f^(p-1)) mod p, only if height != 1
      iters_out (max_h-1) x C(4p-1,3): row h-2 = the iterate g_h, for the rows computed
    height_out: device, 1 int8 (the same code qfs_heights writes).  form = QFS_FORM_* | (QFS_POWER_* << 8); with the
-   identity power mode G_out is left untouched (that route never forms G).  Synchronous. */
+   identity power mode G_out is left untouched (that route never forms G); with the reduced mode G_out and
+   delta_out are left untouched.  Synchronous. */
 int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
                      int32_t *delta_out, int32_t *iters_out, int8_t *height_out);
 

@@ -261,7 +261,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   int engine = opts && opts->engine >= 0 ? opts->engine : QFS_ENGINE_FUSED;
   if (!form_supported(form) || (engine != QFS_ENGINE_FUSED && engine != QFS_ENGINE_STAGED)) return QFS_ERR_FORM;
   const int power = opts && opts->power >= 0 ? opts->power : QFS_POWER_CHAIN;
-  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY) return QFS_ERR_FORM;
+  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY && power != QFS_POWER_REDUCED) return QFS_ERR_FORM;
   if (engine == QFS_ENGINE_STAGED && (form != QFS_FORM_DP4A || power != QFS_POWER_CHAIN)) return QFS_ERR_FORM;
   if (n_items == 0) return QFS_OK;
 
@@ -503,7 +503,7 @@ extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int for
                                 int32_t *delta_out, int32_t *iters_out, int8_t *height_out) {
   const int power = form >> 8;
   form &= 0xFF;
-  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY) return QFS_ERR_FORM;
+  if (power != QFS_POWER_CHAIN && power != QFS_POWER_IDENTITY && power != QFS_POWER_REDUCED) return QFS_ERR_FORM;
   if (!valid_p(p)) return QFS_ERR_INVALID_P;
   if (max_h < 1 || max_h > 10) return QFS_ERR_INVALID_MAX_H;
   if (!coeffs || !height_out) return QFS_ERR_NULL;

@@ -117,8 +117,21 @@ __host__ __device__ inline int chain_slot_words(int p, TileConfig tc) {
 
 __host__ __device__ inline int theta_ring_words_for(int p);
 
+// Ring words the identity and reduced power modes need: three byte arrays (f^(p-2), Delta_1(f), E), and in the
+// reduced mode a product to degree 4p whose own slot ring starts after f^(p-2), Delta_1(f) and q.
+__host__ __device__ inline int aux_ring_words(int p, TileConfig tc) {
+  const int l_fpm2 = tet(4 * (p - 2) + 1), l_d1f = tet(4 * p + 1), l_E = tet(4 * (p - 1) + 1);
+  const int ring_off = (((l_fpm2 + l_d1f + 3) / 4 + 64) + 3) & ~3;
+  int chain = 0;
+  for (int s0 = 0; s0 <= 4 * p; s0 += 32) {
+    const ChainTile T = chain_tile(s0, 4 * p, tc);
+    chain = max(chain, T.nslot * T.slot_words);
+  }
+  return max(ring_off + chain, (l_fpm2 + l_d1f + l_E + 3) / 4);
+}
+
 __host__ __device__ inline int ring_words_for(int p, TileConfig tc) {
-  return max(chain_slot_words(p, tc), theta_ring_words_for(p));
+  return max(max(chain_slot_words(p, tc), theta_ring_words_for(p)), aux_ring_words(p, tc));
 }
 
 __host__ __device__ inline size_t smem_bytes_for(int p, TileConfig tc) {
@@ -896,6 +909,120 @@ __device__ __noinline__ uint32_t *power_identity(Smem &sm, const uint8_t *gs, ui
   return delta;
 }
 
+// ------------------------------------------------------------------------------------------------ reduced theta
+// Heights without Delta_1(f^(p-1)) (power mode QFS_POWER_REDUCED).  From f~^p = A + p Delta_1(f) and the
+// semilinearity of u over p-th powers (Algorithm 2 moves x^(pJ) out as x^J), every iterate F that the loop applies
+// theta to has F[witness] = 0, and for such F
+//     theta(F) = u(F Delta_1(f^(p-1))) = - f^(p-2) u(F Delta_1(f))   (mod p),
+// where u(F Delta_1(f)) is a quartic.  One step costs about 2e5 MACs at p = 7 instead of 6.8e6, and neither
+// G nor the 819k-entry Delta is formed.  Same heights as the other modes (the oracle's route R is this identity).
+template <int P>
+__device__ __forceinline__ int cone_index(int u, int s, int t) { return tet(u) + tri(s) + t; }
+
+template <int P, int FORM, bool DEBUG>
+__device__ __noinline__ int reduced_height(Smem &sm, uint8_t *gs, uint8_t *gn, uint32_t *ring, uint32_t *cur,
+                                           uint32_t *other, int max_h, uint32_t *status, DebugPtrs dbg,
+                                           int &theta_steps) {
+  using Pr = Prime<P>;
+  constexpr int d = Pr::d, dm = 4 * (P - 2), d1 = 4 * P;
+  constexpr int l_fpm2 = tet(dm + 1), l_d1f = tet(d1 + 1);
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
+  uint8_t *fpm2 = reinterpret_cast<uint8_t *>(ring);
+  uint8_t *d1f = fpm2 + l_fpm2;
+  int *q = reinterpret_cast<int *>(ring + (l_fpm2 + l_d1f + 3) / 4 + 1);
+  // f^(p-2) mod p from `other` (degree dm)
+  for (int k = tid; k < sm.SW[dm + 1] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, dm, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(other + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16 && 16 * c + b <= s; ++b)
+      fpm2[tet(u) + tri(s) + 16 * c + b] = (uint8_t)(((w[b >> 2] >> (8 * (b & 3))) & 0xFFu) % P);
+  }
+  __syncthreads();
+  // f~^p = f~^(p-1) f~ (mod p^2), then Delta_1(f) = (f~^p - sum a~_I^p x^(pI)) / p mod p
+  // the product's slot ring goes after fpm2, d1f and q, on a 16-byte boundary (16-byte cp.async and loads)
+  constexpr int ring_off = (((l_fpm2 + l_d1f + 3) / 4 + 64) + 3) & ~3;   // same offset as aux_ring_words
+  static_assert(ring_off % 4 == 0, "16-byte aligned ring");
+  chain_step_call<P, FORM, DEBUG>(cur, other, d, sm, ring + ring_off, gs, status, dbg);
+  __syncthreads();
+  bool bad = false;
+  for (int k = tid; k < sm.SW[d1 + 1] / 4; k += nthreads) {
+    int u, s, c;
+    decode_form_chunk(k, d1, sm.SW, u, s, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(other + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int b = 0; b < 16 && 16 * c + b <= s; ++b) {
+      const int t = 16 * c + b;
+      int G = (int)((w[b >> 2] >> (8 * (b & 3))) & 0xFFu);
+      if ((u % P) == 0 && (s % P) == 0 && (t % P) == 0) {
+        G -= sm.powp[sm.taps[tet(u / P) + tri(s / P) + t / P]];
+        if (G < 0) G += Pr::p2;
+      }
+      if (G % P) bad = true;
+      d1f[tet(u) + tri(s) + t] = (uint8_t)(G / P);
+    }
+  }
+  if (bad) atomicOr(status, kStatusInexactDivision);
+  __syncthreads();
+  uint8_t *F = gs, *Fn = gn;
+  for (int h = 2; h <= max_h; ++h) {
+    // q[r] = u(F Delta_1(f))[r] = sum_c Delta_1(f)[p r + (p-1,..,p-1) - c] F[c], r in B_4: one warp per r
+    for (int r = warp; r < 35; r += nwarps) {
+      int ur, sr, tr;
+      decode_packed(r, ur, sr, tr);
+      const int eu0 = P * ur + 3 * (P - 1), es0 = P * sr + 2 * (P - 1), et0 = P * tr + (P - 1);
+      unsigned a = 0;
+      for (int col = lane; col < tri(d + 1); col += 32) {
+        int uc = (int)((sqrtf(8.0f * (float)col + 1.0f) - 1.0f) * 0.5f);
+        while (tri(uc) > col) --uc;
+        while (tri(uc + 1) <= col) ++uc;
+        const int sc = col - tri(uc);
+        const int eu = eu0 - uc, es = es0 - sc;
+        if (eu < 0 || eu > d1 || es < 0 || es > eu) continue;
+        const int tlo = max(0, et0 - es), thi = min(sc, et0);
+        const uint8_t *dcol = d1f + tet(eu) + tri(es) + et0;   // Delta_1(f)(eu, es, et0 - tc) = dcol[-tc]
+        const uint8_t *fcol = F + tet(uc) + tri(sc);
+        for (int tc = tlo; tc <= thi; ++tc) a += (unsigned)dcol[-tc] * fcol[tc];
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) q[r] = (int)(a % P);
+    }
+    __syncthreads();
+    // F_next = -f^(p-2) q  (mod p): a 35-tap product onto B_d
+    bool any = false;
+    for (int e = tid; e < Pr::ld; e += nthreads) {
+      int ue, se, te;
+      decode_packed(e, ue, se, te);
+      int acc = 0;
+      for (int I = 0; I < 35; ++I) {
+        const int qi = q[I];
+        if (!qi) continue;
+        int uI, sI, tI;
+        decode_packed(I, uI, sI, tI);
+        const int u2 = ue - uI, s2 = se - sI, t2 = te - tI;
+        if (t2 < 0 || s2 < t2 || u2 < s2 || u2 > dm) continue;
+        acc += qi * (int)fpm2[tet(u2) + tri(s2) + t2];
+      }
+      int v = -(acc % P);
+      if (v < 0) v += P;
+      Fn[e] = (uint8_t)v;
+      any |= v != 0;
+    }
+    const int nonzero = __syncthreads_or(any ? 1 : 0);
+    theta_steps = h - 1;
+    if (DEBUG)
+      for (int i = tid; i < Pr::ld; i += nthreads) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = Fn[i];
+    if (Fn[Pr::witness] != 0) return h;
+    if (!nonzero) return 0;
+    uint8_t *t = F; F = Fn; Fn = t;
+    __syncthreads();
+  }
+  return 0;
+}
+
 // Runs A1-A7 for one quartic with the CTA's two workspace buffers; returns the height code.
 template <int P, int FORM, bool DEBUG>
 __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem &sm, uint8_t *gs, uint8_t *gn,
@@ -910,6 +1037,8 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   if (DEBUG)
     for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.g[i] = gs[i];
   if (gs[Pr::witness] != 0) return 1;
+  if (power_mode == 2)
+    return reduced_height<P, FORM, DEBUG>(sm, gs, gn, ring, cur, other, max_h, status, dbg, theta_steps);
   // A4 + A5 into `other` or `cur`, whichever the chain's parity leaves last
   constexpr int nsteps = P * (P - 1) - (P - 1);   // products from f~^(p-1) to f~^(p(p-1))
   uint32_t *delta;

@@ -16,8 +16,8 @@ FORM_INT32, FORM_DP4A, FORM_INT8TC = 0, 1, 2
 ENGINE_FUSED, ENGINE_STAGED = 0, 1
 FORMS = {"int32": FORM_INT32, "dp4a": FORM_DP4A, "int8tc": FORM_INT8TC}
 ENGINES = {"fused": ENGINE_FUSED, "staged": ENGINE_STAGED}
-POWER_CHAIN, POWER_IDENTITY = 0, 1
-POWERS = {"chain": POWER_CHAIN, "identity": POWER_IDENTITY}
+POWER_CHAIN, POWER_IDENTITY, POWER_REDUCED = 0, 1, 2
+POWERS = {"chain": POWER_CHAIN, "identity": POWER_IDENTITY, "reduced": POWER_REDUCED}
 MAX_GROUPS = 8
 PRIMES = (3, 5, 7, 11, 13)
 

@@ -333,3 +333,38 @@ def test_cuda_graph_capture_and_replay(qfs):
     g.replay()
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), oracle.heights(p, b))
+
+
+# ------------------------------------------------------------------------------------- reduced theta mode
+@pytest.mark.parametrize("p,n", [(3, 6), (5, 6), (7, 2)])
+def test_reduced_mode_iterates(qfs, p, n):
+    # the reduced step gives the same iterates g_h as u(Delta_1(f^(p-1)) g) (route A), element by element
+    f, h = find_rows(p, 300, 800 + p, lambda x: x >= 2 or x == 0, n)
+    for row in f:
+        ref = oracle.stage_arrays_r(p, row)
+        for form in CORE_FORMS:
+            got = qfs.debug_stages(p, dev_tensor(row), form=form, power="reduced")
+            assert got["h"] == ref["h"]
+            rows = ref["iters"].shape[0]
+            assert np.array_equal(got["iters"].cpu().numpy()[:rows], ref["iters"]), form
+
+
+@pytest.mark.parametrize("p,n", [(3, 1500), (5, 4000), (7, 2000), (11, 200), (13, 60)])
+def test_reduced_mode_heights(qfs, p, n):
+    f = np.concatenate([inputs.dense(p, n, 8500 + p), inputs.sparse(p, n, 8600 + p)])
+    t = dev_tensor(f)
+    want = oracle.heights(p, f)
+    for form in CORE_FORMS:
+        assert np.array_equal(qfs.heights(p, t, form=form, power="reduced").cpu().numpy(), want), form
+    for max_h in (1, 2, 4):
+        assert np.array_equal(qfs.heights(p, t, power="reduced", max_h=max_h).cpu().numpy(),
+                              oracle.heights(p, f, max_h=max_h))
+    assert qfs.read_status() == 0
+
+
+def test_reduced_mode_paper_examples(qfs):
+    for p in (5, 7, 11, 13):
+        sel = [r for r in example_quartics() if r[0] == p]
+        f = np.stack([r[3] for r in sel])
+        want = np.array([r[1] for r in sel], np.int8)
+        assert np.array_equal(qfs.heights(p, dev_tensor(f), power="reduced").cpu().numpy(), want), p
