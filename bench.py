@@ -202,10 +202,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_steps(p, coeffs, form, steps, warmup, engine=None):
+    def timed_steps(p, coeffs, form, steps, warmup, engine=None, power=None):
         out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=dev)
         for _ in range(warmup):
-            qfs.heights(p, coeffs, out=out, form=form, engine=engine)
+            qfs.heights(p, coeffs, out=out, form=form, engine=engine, power=power)
         torch.cuda.synchronize()
         qfs.read_stats()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -214,7 +214,7 @@ def run_ours(args):
         for i in range(steps):
             flush.fill_(i & 0xFF)                # L2 flush between timed steps, outside the events
             ev[i][0].record(stream)
-            qfs.heights(p, coeffs, out=out, form=form, engine=engine)
+            qfs.heights(p, coeffs, out=out, form=form, engine=engine, power=power)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -303,6 +303,21 @@ def run_ours(args):
                         for o, (p_, f_) in zip(outs5, groups5))
         extra["mixed-p5-p7-p11-pgl4"] = {"value": round(world * n5tot / (ms5 / 1e3), 1), "ms_per_step": round(ms5, 3),
                                          "quartics": n5tot, "pgl4_invariant": bool(invariant)}
+        # the other power modes on the headline workload (bit-identical heights; the reduced mode never forms
+        # Delta_1(f^(p-1)), see include/qfs.h)
+        for power in ("identity", "reduced"):
+            om, per_m, sm_, tm_ = timed_steps(p, coeffs, args.form, max(2, args.steps // 2), args.warmup,
+                                              power=power)
+            msm = max_over_ranks(statistics.mean(per_m))
+            extra[workload_name(HEADLINE_CFG) + f" power={power}"] = {
+                "value": round(world * n / (msm / 1e3), 1), "ms_per_step": round(msm, 3),
+                "bit_exact_vs_chain": bool(np.array_equal(om.cpu().numpy(), heights_np))}
+        o3r, per3r, _, _ = timed_steps(p3, c3, args.form, max(2, args.steps // 2), args.warmup, power="reduced")
+        ms3r = max_over_ranks(statistics.mean(per3r))
+        extra[workload_name(3) + " power=reduced"] = {"value": round(world * n3 / (ms3r / 1e3), 1),
+                                                      "ms_per_step": round(ms3r, 3),
+                                                      "bit_exact_vs_chain": bool(np.array_equal(o3r.cpu().numpy(),
+                                                                                                o3.cpu().numpy()))}
         os_, per_s, ss, ts = timed_steps(p, coeffs, "dp4a", 2, args.warmup, engine="staged")
         extra[workload_name(HEADLINE_CFG) + " staged engine"] = {
             "value": round(world * n / (max_over_ranks(statistics.mean(per_s)) / 1e3), 1),
