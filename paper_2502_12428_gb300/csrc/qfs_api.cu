@@ -121,13 +121,13 @@ int run_staged(DeviceState &S, const FusedParams &prm, const qfs_options_t *opts
     if (e != cudaSuccess) return cuda_fail(e);
     int64_t grid = (int64_t)S.sms * std::max(1, opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : blocks);
     if (opts && opts->max_ctas > 0) grid = std::min<int64_t>(grid, opts->max_ctas);
-    pl.ws_words = (size_t)padded_words(4 * p * (p - 1));
+    pl.ws_words = workspace_stride_words(p);
     const size_t per_cta = 2 * pl.ws_words * sizeof(uint32_t);
     const size_t budget = opts && opts->workspace_budget ? opts->workspace_budget : default_budget(S);
     grid = std::min<int64_t>(grid, (int64_t)(budget / 2 / per_cta));
     if (grid < 1) return QFS_ERR_NO_MEMORY;
     pl.grid = (int)grid;
-    int rc = ensure_workspace(S, (size_t)grid * per_cta);
+    int rc = ensure_workspace(S, workspace_words(grid, pl.ws_words) * sizeof(uint32_t));
     if (rc) return rc;
     const size_t per_surv = staged_survivor_bytes(p);
     int64_t chunk = std::min<int64_t>({g.n, (int64_t)8192, (int64_t)((budget / 2) / per_surv)});
@@ -191,7 +191,7 @@ struct Plan {
 int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_options_t *opts, Plan &plan,
               size_t smem) {
   plan.smem = smem;
-  plan.ws_words = (size_t)padded_words(4 * max_p * (max_p - 1));
+  plan.ws_words = workspace_stride_words(max_p);
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
   if (per_sm == 0) {
     int blocks = 0;
@@ -207,7 +207,7 @@ int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_op
   grid = std::min<int64_t>(grid, n_items);
   if (grid < 1) return QFS_ERR_NO_MEMORY;
   plan.grid = (int)grid;
-  return ensure_workspace(S, (size_t)grid * per_cta);
+  return ensure_workspace(S, workspace_words(grid, plan.ws_words) * sizeof(uint32_t));
 }
 
 }  // namespace
@@ -301,7 +301,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   // shared memory: the largest iterate pair of the launch plus the largest ring any group's tile needs
   int ring_words = 0;
   for (int i = 0; i < prm.n_groups; ++i)
-    ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p)));
+    ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p), form == QFS_FORM_INT8TC));
   const size_t smem = ring_offset_for(tet(4 * (max_p - 1) + 1)) + 4 * (size_t)ring_words;
   Plan plan;
   rc = make_plan(*S, form, max_p, n_items, opts, plan, smem);
@@ -340,7 +340,7 @@ int qfs_plan_prepare(int p, int64_t n_hint) {
   Plan plan;
   int64_t n = n_hint > 0 ? n_hint : (int64_t)1 << 40;
   for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A, QFS_FORM_INT8TC}) {
-    rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p)));
+    rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p), form == QFS_FORM_INT8TC));
     if (rc) return rc;
   }
   cudaError_t e = cudaDeviceSynchronize();
@@ -523,8 +523,12 @@ extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int for
     cudaFree(A); cudaFree(B); cudaFree(Gp); cudaFree(Dp); cudaFree(gtmp); cudaFree(itmp); cudaFree(SWg);
     return cuda_fail(err);
   };
-  if ((e = cudaMalloc(&A, words * 4)) != cudaSuccess) return fail(e);
-  if ((e = cudaMalloc(&B, words * 4)) != cudaSuccess) return fail(e);
+  // the two workspace buffers, each behind a guard of zero words (one workspace stride each)
+  const size_t stride = workspace_stride_words(p);
+  if ((e = cudaMalloc(&A, stride * 4)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&B, stride * 4)) != cudaSuccess) return fail(e);
+  cudaMemset(A, 0, stride * 4);
+  cudaMemset(B, 0, stride * 4);
   if ((e = cudaMalloc(&Gp, words * 4)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&Dp, words * 4)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&gtmp, ld * 4)) != cudaSuccess) return fail(e);
@@ -539,7 +543,7 @@ extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int for
   cudaMemcpy(SWg, sw.data(), sizeof(int) * (D + 3), cudaMemcpyHostToDevice);
   DebugPtrs dbg{Gp, Dp, gtmp, itmp};
   uint32_t *status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
-  if ((e = form_debug(form, p, coeffs, max_h, height_out, A, B, status, dbg, 0, power)) != cudaSuccess) return fail(e);
+  if ((e = form_debug(form, p, coeffs, max_h, height_out, A + kGuardWords, B + kGuardWords, status, dbg, 0, power)) != cudaSuccess) return fail(e);
   if (G_out) unpad_kernel<<<256, 256>>>(Gp, D, SWg, G_out);
   if (delta_out) unpad_kernel<<<256, 256>>>(Dp, D, SWg, delta_out);
   if (g_out) cudaMemcpy(g_out, gtmp, ld * 4, cudaMemcpyDeviceToDevice);

@@ -16,43 +16,13 @@
 // residue (< p^2) and a coefficient (< p): 35 * 168 * 12 = 70,560 for p = 13, far inside int32 -- every form
 // reduces once per output.  Theta sums at most C(4p-1,3) products below p^2: 20,825 * 144 < 2^31.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include "qfs_layout.cuh"
+#include "qfs_common.cuh"
+#include "qfs_sweep.cuh"
 
 namespace qfs {
-
-constexpr int kThreads = 256;
-constexpr int kMaxUparDecl = 8;
-
-// Status bits (atomicOr into the device status word).
-constexpr uint32_t kStatusInexactDivision = 1u;
-constexpr uint32_t kStatusTheta = 2u;
-
-struct DebugPtrs {
-  uint32_t *G;        // padded, degree D: raw G (mod p^2) before the Delta_1 epilogue
-  uint32_t *delta;    // padded, degree D: Delta (mod p)
-  int32_t *g;         // packed, ld values
-  int32_t *iters;     // packed, (max_h-1) x ld
-};
-
-struct Smem {
-  int SW[kSWLen];
-  int taps[35];           // coefficients of f, packed order (index tet(uI) + tri(sI) + tI)
-  uint32_t tapword[15];   // dp4a tap words per (uI, sI) pair: byte k = a(uI, sI, 3-k)
-  uint32_t pair_mask;     // bit tri(uI)+sI set iff that pair has a nonzero tap
-  int powp[kMaxP];        // c^p mod p^2
-  int slot_tab[2][kMaxUparDecl + 4];  // ring word offsets of the slices a chain round reads (double buffered)
-  uint16_t chunk_tab[32 * 40];        // chain block: flat chunk index -> (column - s0) << 8 | chunk
-  int tile_round, tile_ring;          // chain tile configuration of the current quartic's prime
-  int64_t item;
-  int flag;
-  // followed in dynamic shared memory by two byte arrays of ld entries: g (current iterate) and g_next
-};
-
-// Dynamic shared memory layout: [Smem][g: ld][g_next: ld][pad to 16 B][chain ring].
-__host__ __device__ constexpr size_t ring_offset_for(int max_ld) {
-  return (sizeof(Smem) + 2 * (size_t)max_ld + 15) & ~(size_t)15;
-}
 
 // ------------------------------------------------------------------------------------------------ chain step
 // out := in * f (mod p^2), in of degree m_in, out of degree m_in + 4 (one product of the chain).  When LAST, the
@@ -118,26 +88,33 @@ __host__ __device__ inline int chain_slot_words(int p, TileConfig tc) {
 __host__ __device__ inline int theta_ring_words_for(int p);
 
 // Ring words the identity and reduced power modes need: three byte arrays (f^(p-2), Delta_1(f), E), and in the
-// reduced mode a product to degree 4p whose own slot ring starts after f^(p-2), Delta_1(f) and q.
-__host__ __device__ inline int aux_ring_words(int p, TileConfig tc) {
+// reduced mode a product to degree 4p whose own slot ring (int8 tensor form only) starts after f^(p-2),
+// Delta_1(f) and q.
+__host__ __device__ inline int aux_ring_words(int p, TileConfig tc, bool ring_chain) {
   const int l_fpm2 = tet(4 * (p - 2) + 1), l_d1f = tet(4 * p + 1), l_E = tet(4 * (p - 1) + 1);
   const int ring_off = (((l_fpm2 + l_d1f + 3) / 4 + 64) + 3) & ~3;
   int chain = 0;
-  for (int s0 = 0; s0 <= 4 * p; s0 += 32) {
-    const ChainTile T = chain_tile(s0, 4 * p, tc);
-    chain = max(chain, T.nslot * T.slot_words);
-  }
+  if (ring_chain)
+    for (int s0 = 0; s0 <= 4 * p; s0 += 32) {
+      const ChainTile T = chain_tile(s0, 4 * p, tc);
+      chain = max(chain, T.nslot * T.slot_words);
+    }
   return max(ring_off + chain, (l_fpm2 + l_d1f + l_E + 3) / 4);
 }
 
-__host__ __device__ inline int ring_words_for(int p, TileConfig tc) {
-  return max(max(chain_slot_words(p, tc), theta_ring_words_for(p)), aux_ring_words(p, tc));
+// Shared-memory ring words for prime p: the chain's slice ring (only the int8 tensor form stages slices in shared
+// memory; the dp4a and int32 forms sweep them from global memory), theta's Delta slots, and the power modes'
+// arrays.  ring_chain = true gives the size every form fits in.
+__host__ __device__ inline int ring_words_for(int p, TileConfig tc, bool ring_chain = true) {
+  return max(max(ring_chain ? chain_slot_words(p, tc) : 0, theta_ring_words_for(p)), aux_ring_words(p, tc, ring_chain));
 }
 
-__host__ __device__ inline size_t smem_bytes_for(int p, TileConfig tc) {
-  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)ring_words_for(p, tc);
+__host__ __device__ inline size_t smem_bytes_for(int p, TileConfig tc, bool ring_chain = true) {
+  return ring_offset_for(tet(4 * (p - 1) + 1)) + 4 * (size_t)ring_words_for(p, tc, ring_chain);
 }
-__host__ __device__ inline size_t smem_bytes_for(int p) { return smem_bytes_for(p, default_tile(p)); }
+__host__ __device__ inline size_t smem_bytes_for(int p, bool ring_chain = true) {
+  return smem_bytes_for(p, default_tile(p), ring_chain);
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t *smem, const uint32_t *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -273,9 +250,9 @@ __device__ __forceinline__ void tc_b_fragments(const Smem &sm, uint32_t (&b)[16]
 }
 
 template <int P, int FORM, bool LAST, bool DEBUG>
-__device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
-                                           Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
-                                           DebugPtrs dbg) {
+__device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                int m_in, Smem &sm, uint32_t *ring, const uint8_t *gs,
+                                                uint32_t *status, DebugPtrs dbg) {
   using Pr = Prime<P>;
   const int m_out = m_in + 4;
   const uint32_t mask = sm.pair_mask;
@@ -465,101 +442,254 @@ __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint
   if (bad) atomicOr(status, kStatusInexactDivision);
 }
 
-// ------------------------------------------------------------------------------------------------ theta
-// g_next[r] = sum over c in B_d of Delta[p r + (p-1)1 - c] * g[c] mod p, for every r in B_d.  In (u,s,t)
-// coordinates the Delta index is (p u_r + 3(p-1) - u_c, p s_r + 2(p-1) - s_c, p t_r + (p-1) - t_c) and a term is
-// present iff that index lies in the degree-D cone.  Returns true iff some output is nonzero.
-template <int P>
-__device__ __forceinline__ bool theta_step(const uint8_t *__restrict__ delta, const Smem &sm,
-                                           const uint8_t *__restrict__ g, uint8_t *__restrict__ gn) {
-  using Pr = Prime<P>;
-  bool any = false;
-  for (int r = threadIdx.x; r < Pr::ld; r += blockDim.x) {
-    int ur, sr, tr;
-    decode_packed(r, ur, sr, tr);
-    const int eu0 = P * ur + 3 * (P - 1), es0 = P * sr + 2 * (P - 1), et0 = P * tr + (P - 1);
-    int acc = 0;
-    for (int uc = 0; uc <= Pr::d; ++uc) {
-      const int eu = eu0 - uc;
-      if (eu < 0) break;
-      if (eu > Pr::D) continue;
-      for (int sc = 0; sc <= uc; ++sc) {
-        const int es = es0 - sc;
-        if (es < 0) break;
-        if (es > eu) continue;
-        const int tlo = max(0, et0 - es), thi = min(sc, et0);
-        if (tlo > thi) continue;
-        const uint8_t *dcol = delta + 4 * (sm.SW[eu] + colw(es)) + et0;  // Delta(eu, es, et0 - tc) = dcol[-tc]
-        const uint8_t *gcol = g + tet(uc) + tri(sc);
-        for (int tc = tlo; tc <= thi; ++tc) acc += (int)dcol[-tc] * (int)gcol[tc];
-      }
-    }
-    const int v = acc % P;
-    gn[r] = (uint8_t)v;
-    any |= (v != 0);
-  }
-  return any;
+// One product of the chain.  The dp4a and int32 forms sweep the input slices lane by lane (qfs_sweep.cuh); the
+// int8 tensor form runs its tiles over the shared-memory slice ring above.
+template <int P, int FORM, bool LAST, bool DEBUG>
+__device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
+                                           Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
+                                           DebugPtrs dbg) {
+  if constexpr (FORM == 2)
+    ring_chain_step<P, FORM, LAST, DEBUG>(in, out, m_in, sm, ring, gs, status, dbg);
+  else
+    sweep_chain_step<P, FORM, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);
 }
 
-// Theta with Delta streamed through shared memory (p <= 7).  Round e_u loads Delta slice e_u (16-byte cp.async,
-// double buffered) and serves every pair (output slice u_r, g slice u_c) with p u_r + 3(p-1) - u_c = e_u, so each
-// Delta slice is read once per step.  In shared memory every Delta column sits between two 32-byte zero guards and
-// every g column is stored reversed (R[j] = g[s_c - j], zero padded to whole words): the inner product of output
-// (s_r, t_r) with g column (u_c, s_c) is then sum_k dp4a(Delta bytes A+4k .. A+4k+3, R word k) with
-// A = p t_r + (p-1) - s_c, over the whole padded column -- indices outside the column land on zeros.
-// Partial sums accumulate in a shared int32 array, one owner thread per output and round.
-template <int P>
-__host__ __device__ constexpr bool theta_in_smem() { return P <= 7; }
+// ------------------------------------------------------------------------------------------------ theta
+// g_next[r] = sum over c in B_d of Delta[p r + (p-1)1 - c] * g[c] mod p, for every r in B_d (Algorithm 2's u
+// applied to Delta g, only at the outputs u keeps).  In (u,s,t) coordinates the Delta index is
+// (p u_r + 3(p-1) - u_c, p s_r + 2(p-1) - s_c, p t_r + (p-1) - t_c) and a term is present iff that index lies in
+// the degree-D cone.
+//
+// Layout for theta: a guarded copy of Delta in which every column keeps kThetaGuardWords zero words on each side
+// (slice eu starts at word theta_gsw(eu) = SW[eu] + 6 eu (eu + 3); column es of it at + 12 (es + 1) + colw(es)).
+// For output r and g column (u_c, s_c) the terms are then one run of bytes of one Delta column, read against g's
+// column reversed: sum_j Delta[e_u, e_s, A + j] R[j] with A = p t_r + (p-1) - s_c and R[j] = g[u_c, s_c, s_c - j]
+// (zero past s_c).  A is at least -3(p-1) and the run ends at most 3p + 7 bytes past the column's data, inside the
+// guards, so the dot product needs no bounds checks: bytes outside the column are zero.
+constexpr int kThetaGuardWords = 12;   // 48 bytes on each side of every column (p <= 13)
 
+__host__ __device__ constexpr int theta_gsw_extra(int eu) { return 6 * eu * (eu + 3); }
+// words of a degree-D guarded Delta
+inline size_t theta_guarded_words(int p) {
+  const int D = 4 * p * (p - 1);
+  return (size_t)host_sw(D + 1) + (size_t)theta_gsw_extra(D + 1);
+}
+
+// Workspace buffer stride (see qfs_common.cuh): a padded degree-D form, or for p >= 11 theta's guarded copy of
+// Delta, which is larger (p <= 7 streams Delta through shared memory instead).
+inline size_t workspace_stride_words(int p) {
+  const size_t padded = (size_t)padded_words(4 * p * (p - 1));
+  return (p <= 7 ? padded : std::max(padded, theta_guarded_words(p))) + kGuardWords;
+}
+
+// Reversed g columns: column (u_c, s_c) holds g[u_c, s_c, s_c - j] at byte j (j <= s_c), zero-padded to whole words.
+// rcolw(s) = words of the reversed columns 0 .. s-1 of one slice.
 __host__ __device__ constexpr int rcolw(int s) { return ((s >> 2) + 1) * (2 * (s >> 2) + (s & 3)); }
 
 template <int P>
-struct ThetaSmem {
-  static constexpr int d = 4 * (P - 1), D = 4 * P * (P - 1);
-  static constexpr int kGuard = 32;
-  // byte offset of Delta column e_s inside a slot (data after the leading guard)
-  static __host__ __device__ constexpr int col_off(int es) { return 16 * chunk_prefix(es) + kGuard * es + kGuard; }
-  static constexpr int slot_bytes = 16 * chunk_prefix(D + 1) + kGuard * (D + 1) + kGuard;   // + trailing guard
-  static constexpr int slot_words = slot_bytes / 4;
-  static constexpr int rwords = 0;
-};
-
+__host__ __device__ constexpr int theta_r_words() {
+  int r = 0;
+  for (int u = 0; u <= 4 * (P - 1); ++u) r += rcolw(u + 1);
+  return r;
+}
+// Theta for p <= 7 streams Delta slice by slice through shared memory (two guarded slice slots); larger primes
+// gather from the guarded copy in global memory (a slice of Delta does not fit twice in shared memory).
+template <int P>
+__host__ __device__ constexpr bool theta_streams() { return P <= 7; }
+// a slice slot: columns 0 .. D with the guards of the guarded layout
+template <int P>
+__host__ __device__ constexpr int theta_slot_words() { return kThetaGuardWords * (4 * P * (P - 1) + 2) + colw(4 * P * (P - 1) + 1); }
+// shared-memory words theta uses in the ring: reversed g columns and their slice table; when streaming also two
+// slice slots, int32 accumulators, the chunk-to-slot table and the unpacked output coordinates
+// slice slots of the streamed theta: a deeper ring where slots are small (prefetch distance slots - 1)
+template <int P>
+__host__ __device__ constexpr int theta_nslots() { return P <= 5 ? 4 : 2; }
+// word offset of the slice slots in the ring (16-byte aligned for cp.async)
+template <int P>
+__host__ __device__ constexpr int theta_slots_off() { return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3; }
 template <int P>
 __host__ __device__ constexpr int theta_ring_words() {
-  // two Delta slots, the reversed g columns, the int32 accumulators and the reversed-column slice table
-  using T = ThetaSmem<P>;
-  int r = 0;
-  for (int u = 0; u <= T::d; ++u) r += rcolw(u + 1);
-  return 2 * T::slot_words + r + tet(T::d + 1) + (T::d + 2);
+  constexpr int d = 4 * (P - 1), D = 4 * P * (P - 1), ld = tet(d + 1);
+  return theta_slots_off<P>() +
+         (theta_streams<P>() ? theta_nslots<P>() * theta_slot_words<P>() + ld + chunk_prefix(D + 1) + ld + D + 1 : 0);
 }
 
+__host__ __device__ inline int theta_ring_words_for(int p) {
+  switch (p) {
+    case 3: return theta_ring_words<3>();
+    case 5: return theta_ring_words<5>();
+    case 7: return theta_ring_words<7>();
+    case 11: return theta_ring_words<11>();
+    default: return theta_ring_words<13>();
+  }
+}
+
+// Padded Delta (degree D) -> guarded copy.  One thread per 16-byte chunk; the thread of a column's first chunk
+// writes the guard before the column, the thread of a slice's last chunk the guard after it.  The caller
+// synchronises the CTA afterwards.
 template <int P>
-__device__ __noinline__ bool theta_step_smem(const uint32_t *__restrict__ delta, const Smem &sm,
-                                                const uint8_t *__restrict__ g, uint8_t *__restrict__ gn,
-                                                uint32_t *ring) {
+__device__ __forceinline__ void delta_to_guarded(const uint32_t *__restrict__ delta, uint32_t *__restrict__ dg,
+                                                 const Smem &sm) {
+  constexpr int D = Prime<P>::D;
+  const int nchunks = sm.SW[D + 1] / 4;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
+    int u, s, c;
+    decode_form_chunk(k, D, sm.SW, u, s, c);
+    const int o = sm.SW[u] + theta_gsw_extra(u) + kThetaGuardWords * (s + 1) + colw(s) + 4 * c;
+    *reinterpret_cast<uint4 *>(dg + o) = *reinterpret_cast<const uint4 *>(delta + 4 * k);
+    if (c == 0)
+#pragma unroll
+      for (int w = 0; w < kThetaGuardWords; w += 4) *reinterpret_cast<uint4 *>(dg + o - kThetaGuardWords + w) = z;
+    if (s == u && c == chunks_of(s) - 1)
+#pragma unroll
+      for (int w = 0; w < kThetaGuardWords; w += 4) *reinterpret_cast<uint4 *>(dg + o + 4 + w) = z;
+  }
+}
+
+// One theta step: g (shared, packed) -> gn (shared, packed), Delta guarded in global memory.  One thread per
+// output; returns whether some output is nonzero (same value in every thread).
+template <int P>
+__device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const Smem &sm,
+                                          const uint8_t *__restrict__ g, uint8_t *__restrict__ gn, uint32_t *ring) {
   using Pr = Prime<P>;
-  using T = ThetaSmem<P>;
   constexpr int d = Pr::d, D = Pr::D;
   const int tid = threadIdx.x, nthreads = blockDim.x;
-  uint32_t *slots = ring;                                   // 2 x slot_words
-  uint32_t *R = ring + 2 * T::slot_words;                   // reversed g columns
-  int rwords = 0;
-  for (int u = 0; u <= d; ++u) rwords += rcolw(u + 1);
-  int *acc = reinterpret_cast<int *>(R + rwords);           // ld int32
-  int *RSW = acc + Pr::ld;                                  // d+2 slice offsets (words) of R
-  // zero the guards of both slots (fetches never write them), the accumulators; build R
-  for (int i = tid; i < 2 * T::slot_words; i += nthreads) slots[i] = 0;
-  for (int i = tid; i < Pr::ld; i += nthreads) acc[i] = 0;
+  uint32_t *R = ring;
+  int *RSW = reinterpret_cast<int *>(ring + theta_r_words<P>());   // d+2 slice offsets (words) of R
   if (tid == 0) {
     int a = 0;
     for (int u = 0; u <= d + 1; ++u) { RSW[u] = a; a += rcolw(u + 1); }
   }
   __syncthreads();
-  for (int i = tid; i < rwords; i += nthreads) {
-    // word i of R: find its column (u_c, s_c) and word k
+  for (int i = tid; i < theta_r_words<P>(); i += nthreads) {
     int u = 0;
     while (RSW[u + 1] <= i) ++u;
-    int rem = i - RSW[u];
+    const int rem = i - RSW[u];
+    int sc = 0;
+    while (rcolw(sc + 1) <= rem) ++sc;
+    const int k = rem - rcolw(sc);
+    const uint8_t *gcol = g + tet(u) + tri(sc);
+    uint32_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * k + b;
+      if (j <= sc) w |= (uint32_t)gcol[sc - j] << (8 * b);
+    }
+    R[i] = w;
+  }
+  __syncthreads();
+  bool any = false;
+  for (int r = tid; r < Pr::ld; r += nthreads) {
+    int ur, sr, tr;
+    decode_packed(r, ur, sr, tr);
+    const int Ue = P * ur + 3 * (P - 1), Se = P * sr + 2 * (P - 1), Te = P * tr + (P - 1);
+    const int uc_lo = max(0, Ue - D), uc_hi = min(d, Ue);
+    unsigned acc = 0;
+    for (int uc = uc_lo; uc <= uc_hi; ++uc) {
+      const int eu = Ue - uc;
+      // g columns s_c with Delta column e_s = Se - s_c in [0, e_u]
+      const int sc_lo = max(0, Se - eu), sc_hi = min(uc, Se);
+      if (sc_lo > sc_hi) continue;
+      int es = Se - sc_lo;
+      // byte of Delta(e_u, e_s, Te - s_c) and word of R(u_c, s_c), both updated as s_c grows
+      int byte = 4 * (sm.SW[eu] + theta_gsw_extra(eu) + kThetaGuardWords * (es + 1) + colw(es)) + Te - sc_lo;
+      const uint32_t *Rc = R + RSW[uc] + rcolw(sc_lo);
+      for (int sc = sc_lo; sc <= sc_hi; ++sc) {
+        const uint32_t *dw = dg + (byte >> 2);
+        const unsigned sh = 8u * (unsigned)(byte & 3);
+        const int nw = (sc >> 2) + 1;   // at most p words
+        // every word of the run is requested before the first is used, so a pair waits on memory once
+        uint32_t dv[P + 1], rv[P];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) dv[k] = k <= nw ? dw[k] : 0u;
+#pragma unroll
+        for (int k = 0; k < P; ++k) rv[k] = k < nw ? Rc[k] : 0u;
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+          if (k < nw) acc = __dp4a(__funnelshift_r(dv[k], dv[k + 1], sh), rv[k], acc);
+        // next g column: e_s - 1, whose guarded column starts 12 + 4 chunks_of(e_s - 1) words earlier
+        Rc += nw;
+        --es;
+        byte -= 4 * (kThetaGuardWords + 4 * chunks_of(es)) + 1;
+      }
+    }
+    const int v = (int)(acc % P);
+    gn[r] = (uint8_t)v;
+    any |= v != 0;
+  }
+  return __syncthreads_or(any ? 1 : 0) != 0;
+}
+
+// One (u_r, s_c) unit of a streamed theta round: lanes take the outputs r0 + lane, r0 + lane + 32, ... < r1 of slice
+// u_r; each sums NW words of its Delta window (guarded slot) against the NW words of g's reversed column s_c.
+// gofs[e_s] = byte offset of Delta column e_s in a slot; rst[r] = u_r | s_r << 8 | t_r << 16.
+template <int P, int NW>
+__device__ __forceinline__ void theta_unit(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rc,
+                                           const int *__restrict__ gofs, const uint32_t *__restrict__ rst,
+                                           int *acc, int r0, int r1, int sc, int lane) {
+  uint32_t rv[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) rv[k] = Rc[k];
+  for (int r = r0 + lane; r < r1; r += 32) {
+    const uint32_t x = rst[r];
+    const int sr = (int)((x >> 8) & 255u), tr = (int)(x >> 16);
+    const int byte = gofs[P * sr + 2 * (P - 1) - sc] + P * tr + (P - 1) - sc;
+    const uint32_t *dw = slot + (byte >> 2);
+    const unsigned sh = 8u * (unsigned)(byte & 3);
+    uint32_t dv[NW + 1];
+#pragma unroll
+    for (int k = 0; k <= NW; ++k) dv[k] = dw[k];
+    unsigned a = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) a = __dp4a(__funnelshift_r(dv[k], dv[k + 1], sh), rv[k], a);
+    atomicAdd(acc + r, (int)a);
+  }
+}
+
+// One theta step with Delta (padded, degree D, global memory) streamed through shared memory, p <= 7.  Round e_u
+// copies slice e_u into a guarded slot (16-byte cp.async, double buffered) and serves every output slice u_r whose
+// g slice u_c = p u_r + 3(p-1) - e_u exists, as warp-wide units (u_r, g column s_c) whose lanes take consecutive
+// outputs and run the same number of words; partial sums go to shared int32 accumulators.  Every Delta byte is read from global memory
+// once per step.  Returns whether some output is nonzero (same value in every thread).
+template <int P>
+__device__ __noinline__ bool theta_stream(const uint32_t *__restrict__ delta, const Smem &sm,
+                                          const uint8_t *__restrict__ g, uint8_t *__restrict__ gn, uint32_t *ring) {
+  using Pr = Prime<P>;
+  constexpr int d = Pr::d, D = Pr::D, ld = Pr::ld;
+  constexpr int SLOT = theta_slot_words<P>();
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
+  uint32_t *R = ring;
+  int *RSW = reinterpret_cast<int *>(ring + theta_r_words<P>());
+  constexpr int NS = theta_nslots<P>();
+  uint32_t *slots = ring + theta_slots_off<P>();                        // NS x SLOT, 16-byte aligned
+  int *acc = reinterpret_cast<int *>(slots + NS * SLOT);
+  int *ctab = acc + ld;                                                 // flat chunk of a slice -> slot word
+  uint32_t *rst = reinterpret_cast<uint32_t *>(ctab + chunk_prefix(D + 1));   // output r -> ur | sr << 8 | tr << 16
+  int *gofs = reinterpret_cast<int *>(rst + ld);                        // column e_s -> byte offset in a slot
+  for (int es = tid; es <= D; es += nthreads) gofs[es] = 4 * (kThetaGuardWords * (es + 1) + colw(es));
+  if (tid == 0) {
+    int a = 0;
+    for (int u = 0; u <= d + 1; ++u) { RSW[u] = a; a += rcolw(u + 1); }
+  }
+  for (int i = tid; i < NS * SLOT; i += nthreads) slots[i] = 0u;
+  for (int i = tid; i < ld; i += nthreads) {
+    acc[i] = 0;
+    int u, s, t;
+    decode_packed(i, u, s, t);
+    rst[i] = (uint32_t)u | ((uint32_t)s << 8) | ((uint32_t)t << 16);
+  }
+  for (int k = tid; k < chunk_prefix(D + 1); k += nthreads) {
+    int es, c;
+    decode_chunk(k, es, c);
+    ctab[k] = kThetaGuardWords * (es + 1) + colw(es) + 4 * c;
+  }
+  __syncthreads();
+  for (int i = tid; i < theta_r_words<P>(); i += nthreads) {
+    int u = 0;
+    while (RSW[u + 1] <= i) ++u;
+    const int rem = i - RSW[u];
     int sc = 0;
     while (rcolw(sc + 1) <= rem) ++sc;
     const int k = rem - rcolw(sc);
@@ -573,79 +703,61 @@ __device__ __noinline__ bool theta_step_smem(const uint32_t *__restrict__ delta,
     R[i] = w;
   }
   auto fetch = [&](int eu, int buf) {
-    uint8_t *dst = reinterpret_cast<uint8_t *>(slots + buf * T::slot_words);
+    uint32_t *dst = slots + buf * SLOT;
     const uint32_t *src = delta + sm.SW[eu];
-    // column es: chunks_of(es) chunks at col_off(es); the flat chunk index runs over the slice
-    const int nchunks = chunk_prefix(eu + 1);
-    for (int i = tid; i < nchunks; i += nthreads) {
-      int es, c;
-      decode_chunk(i, es, c);
-      cp_async16(reinterpret_cast<uint32_t *>(dst + T::col_off(es) + 16 * c), src + 4 * i, true);
-    }
+    const int n = chunk_prefix(eu + 1);
+    for (int k = tid; k < n; k += nthreads) cp_async16(dst + ctab[k], src + 4 * k, true);
   };
-  __syncthreads();
-  fetch(0, 0);
-  cp_async_commit();
-  for (int eu = 0; eu <= D; ++eu) {
-    if (eu + 1 <= D) fetch(eu + 1, (eu + 1) & 1);
+  // slices 0 .. NS-2 in flight; round e_u waits for its own slice, then refills the slot round e_u - 1 used
+  for (int e = 0; e < NS - 1; ++e) {
+    if (e <= D) fetch(e, e);
     cp_async_commit();
-    asm volatile("cp.async.wait_group 1;\n" ::);
-    __syncthreads();
-    const uint8_t *dsl = reinterpret_cast<const uint8_t *>(slots + (eu & 1) * T::slot_words);
-    // output slices served by this round: u_c = p u_r + 3(p-1) - eu in [0, d]
-    const int ur_lo = max(0, (eu - 3 * (P - 1) + P - 1) / P);
-    const int ur_hi = min(d, (eu - 3 * (P - 1) + d) / P);
-    int total = 0;
-    for (int ur = ur_lo; ur <= ur_hi; ++ur) total += tri(ur + 1);
-    for (int item = tid; item < total; item += nthreads) {
-      int ur = ur_lo, f = item;
-      while (f >= tri(ur + 1)) { f -= tri(ur + 1); ++ur; }
-      int sr = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
-      while (tri(sr) > f) --sr;
-      while (tri(sr + 1) <= f) ++sr;
-      const int tr = f - tri(sr);
-      const int uc = P * ur + 3 * (P - 1) - eu;
-      const int E = P * tr + (P - 1);
-      const uint32_t *Rs = R + RSW[uc];
-      unsigned a = 0;
-      for (int sc = 0; sc <= uc; ++sc) {
-        const int es = P * sr + 2 * (P - 1) - sc;
-        if (es < 0) break;
-        if (es > eu) continue;
-        const int base = T::col_off(es) + E - sc;           // byte of Delta(eu, es, A) with A = E - sc >= -(3p-3)
-        const uint32_t *dw = reinterpret_cast<const uint32_t *>(dsl) + (base >> 2);
-        const unsigned sel = (unsigned)(base & 3);
-        const unsigned perm = (sel == 0) ? 0x3210u : (sel == 1) ? 0x4321u : (sel == 2) ? 0x5432u : 0x6543u;
-        const uint32_t *Rc = Rs + rcolw(sc);
-        const int nw = (sc >> 2) + 1;
-        uint32_t lo = dw[0];
-        for (int k = 0; k < nw; ++k) {
-          const uint32_t hi = dw[k + 1];
-          a = __dp4a(__byte_perm(lo, hi, perm), Rc[k], a);
-          lo = hi;
-        }
+  }
+  for (int eu = 0; eu <= D; ++eu) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));
+    __syncthreads();   // slot eu % NS is complete for every thread; slot (eu - 1) % NS is no longer read
+    if (eu + NS - 1 <= D) fetch(eu + NS - 1, (eu + NS - 1) % NS);
+    cp_async_commit();
+    const uint32_t *slot = slots + (eu % NS) * SLOT;
+    // output slices with u_c = p u_r + 3(p-1) - e_u in [0, d]
+    const int base = eu - 3 * (P - 1);
+    const int ur_lo = max(0, (base + P - 1) / P);
+    const int ur_hi = min(d, base + d >= 0 ? (base + d) / P : -1);
+    if (ur_lo > ur_hi) continue;
+    // work units (u_r, s_c), one warp each: the outputs of slice u_r whose Delta column e_s = p s_r + 2(p-1) - s_c
+    // lies in slice e_u, a contiguous run of packed outputs; every lane of the unit runs the same word count
+    int nunits = 0;
+    for (int ur = ur_lo; ur <= ur_hi; ++ur) nunits += P * ur - base + 1;   // s_c = 0 .. u_c
+    for (int unit = warp; unit < nunits; unit += nwarps) {
+      int ur = ur_lo, sc = unit;
+      while (sc > P * ur - base) { sc -= P * ur - base + 1; ++ur; }
+      const int uc = P * ur - base;
+      const int sr_lo = max(0, sc - 2 * (P - 1) > 0 ? (sc - 2 * (P - 1) + P - 1) / P : 0);
+      const int nhi = eu + sc - 2 * (P - 1);   // e_s <= e_u  <=>  p s_r <= nhi
+      const int sr_hi = min(ur, nhi >= 0 ? nhi / P : -1);
+      if (sr_lo > sr_hi) continue;
+      const uint32_t *Rc = R + RSW[uc] + rcolw(sc);
+      const int r0 = tet(ur) + tri(sr_lo), r1 = tet(ur) + tri(sr_hi + 1);
+      switch (sc >> 2) {   // words of g's reversed column s_c: s_c / 4 + 1 <= p
+        case 0: theta_unit<P, 1>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        case 1: theta_unit<P, 2>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        case 2: theta_unit<P, 3>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        case 3: theta_unit<P, 4>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        case 4: theta_unit<P, 5>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        case 5: theta_unit<P, 6>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+        default: theta_unit<P, 7>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
       }
-      acc[tet(ur) + f] += (int)a;
     }
-    __syncthreads();
   }
   cp_async_wait_all();
+  __syncthreads();
   bool any = false;
-  for (int i = tid; i < Pr::ld; i += nthreads) {
-    const int v = acc[i] % P;
-    gn[i] = (uint8_t)v;
+  for (int r = tid; r < ld; r += nthreads) {
+    const int v = acc[r] % P;
+    gn[r] = (uint8_t)v;
     any |= v != 0;
   }
-  return any;
-}
-
-__host__ __device__ inline int theta_ring_words_for(int p) {
-  switch (p) {
-    case 3: return theta_ring_words<3>();
-    case 5: return theta_ring_words<5>();
-    case 7: return theta_ring_words<7>();
-    default: return 0;
-  }
+  return __syncthreads_or(any ? 1 : 0) != 0;
 }
 
 // ------------------------------------------------------------------------------------------------ one quartic
@@ -749,19 +861,6 @@ __device__ __forceinline__ void power_to_G(Smem &sm, const uint8_t *gs, uint32_t
   __syncthreads();
 }
 
-// One theta step on g (shared) into gn (shared), Delta in global memory (padded, degree D).  Returns whether some
-// output is nonzero (same value in every thread).
-template <int P>
-__device__ __forceinline__ bool theta_any(const uint32_t *delta, Smem &sm, const uint8_t *g, uint8_t *gn,
-                                          uint32_t *ring) {
-  bool any;
-  if constexpr (theta_in_smem<P>())
-    any = theta_step_smem<P>(delta, sm, g, gn, ring);
-  else
-    any = theta_step<P>(reinterpret_cast<const uint8_t *>(delta), sm, g, gn);
-  return __syncthreads_or(any ? 1 : 0) != 0;
-}
-
 // ------------------------------------------------------------------------------------------------ identity power
 // A4 + A5 by an exact algebraic shortcut (power mode QFS_POWER_IDENTITY).  It produces the same Delta_1(f^(p-1))
 // array as the chain, and the chain stays the literal reading of Algorithm 1.
@@ -832,7 +931,9 @@ __device__ __noinline__ uint32_t *power_identity(Smem &sm, const uint8_t *gs, ui
       }
     sm.pair_mask = mask;
   }
-  uint32_t *pa = cur, *pb = cur + sm.SW[d + 1];
+  // pa = cur, pb after pa's largest form and a guard of zero words (chain products read from both)
+  uint32_t *pa = cur, *pb = cur + sm.SW[d + 1] + kGuardWords;
+  if (tid < kGuardWords) pb[tid - kGuardWords] = 0u;
   for (int k = tid; k < sm.SW[5] / 4; k += nthreads) {
     int u, s, c;
     decode_form_chunk(k, 4, sm.SW, u, s, c);
@@ -1050,10 +1151,17 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   }
   if (DEBUG)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
-  // A6 + A7
+  // A6 + A7.  p <= 7: Delta streams through shared memory; larger p: a guarded copy of Delta, built in the buffer
+  // that does not hold Delta, is gathered from directly
+  uint32_t *dg = delta == bufA ? bufB : bufA;
+  if (!theta_streams<P>()) {
+    delta_to_guarded<P>(delta, dg, sm);
+    __syncthreads();
+  }
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
-    const bool nonzero = theta_any<P>(delta, sm, g, g2, ring);
+    const bool nonzero = theta_streams<P>() ? theta_stream<P>(delta, sm, g, g2, ring)
+                                            : theta_gather<P>(dg, sm, g, g2, ring);
     theta_steps = h - 1;
     if (DEBUG)
       for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = g2[i];
@@ -1086,9 +1194,9 @@ struct FusedParams {
   unsigned long long *counter;        // work queue head (zeroed before launch)
   uint32_t *status;
   unsigned long long *stats;          // [0] quartics past the height-1 test, [1] theta steps run
-  uint32_t *ws;                       // 2 buffers of ws_words per CTA
+  uint32_t *ws;                       // workspace: a guard, then 2 buffers of ws_words (the stride) per CTA
   size_t ws_words;
-  int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut
+  int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut, 2: reduced theta
 };
 
 template <int FORM>
@@ -1102,8 +1210,9 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
   uint8_t *gn = gs + max_ld;
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(max_ld));
   build_sw(sm.SW, prm.sw_len);
-  uint32_t *bufA = prm.ws + (size_t)blockIdx.x * 2 * prm.ws_words;
-  uint32_t *bufB = bufA + prm.ws_words;
+  init_task_queue(sm);
+  uint32_t *bufA, *bufB;
+  cta_buffers(prm.ws, prm.ws_words, bufA, bufB);
   DebugPtrs dbg{nullptr, nullptr, nullptr, nullptr};
   for (;;) {
     __syncthreads();

@@ -5,12 +5,13 @@
 
 namespace qfs {
 
-#ifndef QFS_MIN_CTAS_PER_SM
-#define QFS_MIN_CTAS_PER_SM 3
-#endif
+// Resident CTAs per SM the register allocation is bounded for: the swept chain (dp4a and int32 forms) keeps five
+// accumulator sets per lane and gets 128 registers (2 CTAs of 256 threads); the int8 tensor form gets 85 (3 CTAs).
+template <int FORM>
+constexpr int min_ctas_per_sm() { return FORM == 2 ? 3 : 2; }
 // Persistent launch: every CTA pulls quartics from a global atomic queue until the queue is empty.
 template <int FORM>
-__global__ void __launch_bounds__(kThreads, QFS_MIN_CTAS_PER_SM) fused_kernel(FusedParams prm) {
+__global__ void __launch_bounds__(kThreads, min_ctas_per_sm<FORM>()) fused_kernel(FusedParams prm) {
   fused_body<FORM>(prm);
 }
 
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int m
   uint8_t *gn = gs + Prime<P>::ld;
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw + ring_offset_for(Prime<P>::ld));
   build_sw(sm.SW, Prime<P>::D + 2);
+  init_task_queue(sm);
   if (threadIdx.x == 0) {
     sm.tile_round = default_tile(P).round_chunks;
     sm.tile_ring = default_tile(P).ring_words;
@@ -70,7 +72,7 @@ struct FormLauncher {
   cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st,     \
                                         int power_mode) {                                                     \
-    const size_t smem = smem_bytes_for(p);                                                                    \
+    const size_t smem = smem_bytes_for(p, FORM == 2);                                                         \
     cudaError_t e = cudaSuccess;                                                                              \
     switch (p) {                                                                                              \
       case 3: QFS_DEBUG_LAUNCH(3, FORM); break;                                                               \

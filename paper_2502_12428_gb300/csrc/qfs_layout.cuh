@@ -10,9 +10,12 @@
 // C(m+3,3) = tet(m+1) entries (the paper's l_d, Sec. 4).
 //
 // Padded layout (device workspaces): the same order, but every column (u, s) -- the s+1 entries t = 0..s, one byte
-// each -- starts on a 16-byte boundary and occupies chunks(s) = s/16 + 1 chunks of four 32-bit words; padding bytes
-// are zero.  Word offset of column (u, s) = SW[u] + 4 F(s), where F(s) = sum_{s' < s} chunks(s') = (q+1)(8q+r) for
-// s = 16q + r, and SW[u] = sum_{v < u} 4 F(v+1).  SW does not depend on m; a degree-m form uses words
+// each -- starts on a 16-byte boundary and occupies chunks(s) = (s+4)/16 + 1 chunks of four 32-bit words; padding
+// bytes are zero.  Sizing a column by s+4 rather than s gives two guarantees that the chain product relies on:
+// the last word of every column is padding (so the word before any column start is zero), and column s - sI
+// (sI <= 4) always has room for words 0 .. s/4 + 1 of column s.  Word offset of column (u, s) = SW[u] + 4 F(s),
+// where F(s) = sum_{s' < s} chunks(s') = E(s+4) - 4 with E(n) = sum_{n' < n} (n'/16 + 1) = (q+1)(8q+r) for
+// n = 16q + r, and SW[u] = sum_{v < u} 4 F(v+1).  SW does not depend on m; a degree-m form uses words
 // [0, SW[m+1]).
 #pragma once
 #include <cstdint>
@@ -21,8 +24,10 @@ namespace qfs {
 
 __host__ __device__ constexpr int tet(int u) { return u * (u + 1) * (u + 2) / 6; }
 __host__ __device__ constexpr int tri(int s) { return s * (s + 1) / 2; }
-__host__ __device__ constexpr int chunks_of(int s) { return (s >> 4) + 1; }
-__host__ __device__ constexpr int chunk_prefix(int s) { return ((s >> 4) + 1) * (8 * (s >> 4) + (s & 15)); }
+__host__ __device__ constexpr int chunks_of(int s) { return ((s + 4) >> 4) + 1; }
+// E(n) = sum_{n' < n} (n'/16 + 1); chunk_prefix(s) = F(s) = E(s + 4) - E(4)
+__host__ __device__ constexpr int chunk_prefix16(int n) { return ((n >> 4) + 1) * (8 * (n >> 4) + (n & 15)); }
+__host__ __device__ constexpr int chunk_prefix(int s) { return chunk_prefix16(s + 4) - 4; }
 // word offset of column s inside its slice (16-byte aligned)
 __host__ __device__ constexpr int colw(int s) { return 4 * chunk_prefix(s); }
 __host__ __device__ constexpr int n_monomials(int m) { return tet(m + 1); }
@@ -65,8 +70,10 @@ __device__ __forceinline__ void build_sw(int *SW, int n) {
   }
 }
 
-// Flat chunk index h of one slice (h = F(s) + c) -> column s and chunk c.
+// Flat chunk index h of one slice (h = F(s) + c) -> column s and chunk c.  F(s) = E(s+4) - 4, so h + 4 is the
+// flat index of chunk c of "column" s + 4 under E, which inverts in closed form.
 __device__ __forceinline__ void decode_chunk(int h, int &s, int &c) {
+  h += 4;
   int q = (int)((sqrtf(1.0f + 0.5f * (float)h) - 1.0f) * 0.5f);
   while (8 * (q + 1) * (q + 2) <= h) ++q;
   while (q > 0 && 8 * q * (q + 1) > h) --q;
@@ -75,7 +82,7 @@ __device__ __forceinline__ void decode_chunk(int h, int &s, int &c) {
   while (rr * (q + 1) > rem) --rr;
   while ((rr + 1) * (q + 1) <= rem) ++rr;
   c = rem - rr * (q + 1);
-  s = 16 * q + rr;
+  s = 16 * q + rr - 4;
 }
 
 // Flat chunk index k of a whole degree-m padded form -> (u, s, c); SW is the slice table (in words).

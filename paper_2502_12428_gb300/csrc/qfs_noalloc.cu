@@ -26,7 +26,7 @@ constexpr size_t kControlBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // The fused persistent kernel (dp4a form), given its workspace in the fixed array instead of a cudaMalloc'd one.
-__global__ void __launch_bounds__(kThreads, 3) noalloc_fused_kernel(FusedParams prm) { fused_body<1>(prm); }
+__global__ void __launch_bounds__(kThreads, 2) noalloc_fused_kernel(FusedParams prm) { fused_body<1>(prm); }
 
 constexpr int kMaxDev = 64;
 void *g_scratch_addr[kMaxDev];   // device address of g_noalloc_scratch on each device, set once
@@ -70,9 +70,9 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   if (n == 0) return QFS_OK;
 
   // Size check first: one persistent CTA needs two buffers that hold a form of degree 4p(p-1).
-  const size_t ws_words = (size_t)padded_words(4 * p * (p - 1));
+  const size_t ws_words = workspace_stride_words(p);
   const size_t per_cta = 2 * ws_words * sizeof(uint32_t);
-  const size_t fit = (kScratchBytes - kControlBytes) / per_cta;
+  const size_t fit = (kScratchBytes - kControlBytes - kGuardWords * sizeof(uint32_t)) / per_cta;
   if (fit < 1) return QFS_ERR_NO_MEMORY;  // p = 13 needs more than the fixed 64 MiB for a single CTA
 
   void *scratch = nullptr;
@@ -80,7 +80,7 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   int rc = scratch_for_current_device(&scratch, &sms);
   if (rc) return rc;
 
-  const size_t smem = smem_bytes_for(p);
+  const size_t smem = smem_bytes_for(p, /*ring_chain=*/false);
   cudaError_t e = cudaFuncSetAttribute(noalloc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return QFS_ERR_CUDA;

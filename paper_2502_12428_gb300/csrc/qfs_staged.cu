@@ -57,11 +57,13 @@ __device__ __forceinline__ void stage_smem(Smem *&sm, uint8_t *&gs, uint8_t *&gn
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 3) stage_fedder(StagedChunk c) {
+__global__ void __launch_bounds__(kThreads, 2) stage_fedder(StagedChunk c) {
   Smem *sm; uint8_t *gs, *gn; uint32_t *ring;
   stage_smem<P>(sm, gs, gn, ring);
   build_sw(sm->SW, Prime<P>::D + 2);
-  uint32_t *bufA = c.ws + (size_t)blockIdx.x * 2 * c.ws_words, *bufB = bufA + c.ws_words;
+  init_task_queue(*sm);
+  uint32_t *bufA, *bufB;
+  cta_buffers(c.ws, c.ws_words, bufA, bufB);
   DebugPtrs dbg{nullptr, nullptr, nullptr, nullptr};
   for (;;) {
     __syncthreads();
@@ -90,15 +92,17 @@ __global__ void __launch_bounds__(kThreads, 3) stage_fedder(StagedChunk c) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 3) stage_power(StagedChunk c) {
+__global__ void __launch_bounds__(kThreads, 2) stage_power(StagedChunk c) {
   using Pr = Prime<P>;
   Smem *sm; uint8_t *gs, *gn; uint32_t *ring;
   stage_smem<P>(sm, gs, gn, ring);
   build_sw(sm->SW, Pr::D + 2);
-  uint32_t *bufA = c.ws + (size_t)blockIdx.x * 2 * c.ws_words, *bufB = bufA + c.ws_words;
+  init_task_queue(*sm);
+  uint32_t *bufA, *bufB;
+  cta_buffers(c.ws, c.ws_words, bufA, bufB);
   DebugPtrs dbg{nullptr, nullptr, nullptr, nullptr};
   const unsigned total = *c.count;
-  const size_t gwords = c.ws_words;  // padded words of degree D
+  const size_t gwords = c.ws_words;  // slot stride (at least the padded words of degree D)
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) sm->item = atomicAdd(c.queue, 1u);
@@ -127,8 +131,8 @@ __global__ void __launch_bounds__(kThreads) stage_delta1(StagedChunk c) {
   }
   __syncthreads();
   const unsigned total = *c.count;
-  const size_t gwords = c.ws_words;  // padded words of degree D
-  const size_t chunks = gwords / 4;
+  const size_t gwords = c.ws_words;            // stride of the G slots
+  const size_t chunks = (size_t)SW[Pr::D + 1] / 4;  // 16-byte chunks of a degree-D form (the slot may be longer)
   bool bad = false;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)total * chunks;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -162,19 +166,28 @@ __global__ void __launch_bounds__(kThreads) stage_delta1(StagedChunk c) {
 
 // One CTA per undecided survivor: g (gin slot) -> theta(g) (gout slot).
 template <int P>
-__global__ void __launch_bounds__(kThreads, 3) stage_theta(StagedChunk c, const uint8_t *gin, uint8_t *gout) {
+__global__ void __launch_bounds__(kThreads, 2) stage_theta(StagedChunk c, const uint8_t *gin, uint8_t *gout) {
   using Pr = Prime<P>;
   Smem *sm; uint8_t *gs, *gn; uint32_t *ring;
   stage_smem<P>(sm, gs, gn, ring);
   build_sw(sm->SW, Pr::D + 2);
+  init_task_queue(*sm);
+  uint32_t *dg, *unused;
+  cta_buffers(c.ws, c.ws_words, dg, unused);  // the guarded copy of the survivor's Delta
   __syncthreads();
   const unsigned total = *c.count;
-  const size_t gwords = c.ws_words;  // padded words of degree D
+  const size_t gwords = c.ws_words;  // slot stride (at least the padded words of degree D)
   for (unsigned slot = blockIdx.x; slot < total; slot += gridDim.x) {
     if (!c.active[slot]) continue;
     for (int i = threadIdx.x; i < Pr::ld; i += blockDim.x) gs[i] = gin[(size_t)slot * Pr::ld + i];
-    __syncthreads();
-    theta_any<P>(c.G + slot * gwords, *sm, gs, gn, ring);
+    if (theta_streams<P>()) {
+      __syncthreads();
+      theta_stream<P>(c.G + slot * gwords, *sm, gs, gn, ring);
+    } else {
+      delta_to_guarded<P>(c.G + slot * gwords, dg, *sm);
+      __syncthreads();
+      theta_gather<P>(dg, *sm, gs, gn, ring);
+    }
     for (int i = threadIdx.x; i < Pr::ld; i += blockDim.x) gout[(size_t)slot * Pr::ld + i] = gn[i];
     if (threadIdx.x == 0) atomicAdd(c.stats + 1, 1ull);
     __syncthreads();
@@ -210,7 +223,7 @@ template <int P>
 cudaError_t run_chunks(const StagedPlan &pl, const uint8_t *coeffs, int8_t *heights, int64_t n, int max_h,
                        cudaStream_t st) {
   using Pr = Prime<P>;
-  const size_t smem = smem_bytes_for(P);
+  const size_t smem = smem_bytes_for(P, /*ring_chain=*/false);
   cudaError_t e;
   for (auto k : {(const void *)stage_fedder<P>, (const void *)stage_power<P>, (const void *)stage_theta<P>}) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -253,7 +266,7 @@ cudaError_t run_chunks(const StagedPlan &pl, const uint8_t *coeffs, int8_t *heig
 
 size_t staged_survivor_bytes(int p) {
   const int ld = tet(4 * (p - 1) + 1);
-  return (size_t)padded_words(4 * p * (p - 1)) * 4 + 2 * (size_t)ld + sizeof(int) + 1;
+  return workspace_stride_words(p) * 4 + 2 * (size_t)ld + sizeof(int) + 1;
 }
 
 cudaError_t staged_run(const StagedPlan &pl, int p, const uint8_t *coeffs, int8_t *heights, int64_t n, int max_h,
@@ -268,7 +281,7 @@ cudaError_t staged_run(const StagedPlan &pl, int p, const uint8_t *coeffs, int8_
 }
 
 cudaError_t staged_occupancy(int p, int *blocks) {
-  const size_t smem = smem_bytes_for(p);
+  const size_t smem = smem_bytes_for(p, /*ring_chain=*/false);
   const void *k = p == 3 ? (const void *)stage_power<3> : p == 5 ? (const void *)stage_power<5>
                 : p == 7 ? (const void *)stage_power<7> : p == 11 ? (const void *)stage_power<11>
                 : (const void *)stage_power<13>;

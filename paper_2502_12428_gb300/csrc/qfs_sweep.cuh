@@ -1,0 +1,317 @@
+// One product of the chain, out = in * f~ (mod p^2), by per-lane sweeps over the input slices (dp4a and int32
+// forms).  Algorithm 1 needs lift(g)^p mod p^2; the chain forms it as f~^(p(p-1)) one multiplication by f~ at a time
+// (see qfs_engine.cuh), and this file is that multiplication.
+//
+// Work item = one half-chunk of an output column: column s of the output slices, outputs t = 8h .. 8h+7 (h is
+// the half-chunk; column s has s/8 + 1 of them).  A lane owns one item for every output slice u and walks the
+// input slices v upwards.  Input slice v feeds output slices u = v .. v+4 (tap pairs uI = u - v): the lane loads
+// the five input columns s - sI (sI = 0..4) of slice v once (eight bytes plus the word before them), builds the
+// byte windows once, and adds every tap pair (uI, sI) with uI >= sI into the accumulator set of output u = v + uI.
+// Five accumulator sets rotate with v mod 5 (the loop is unrolled five ways so that every index is static); after
+// slice v the set of output v is complete and is reduced, packed and stored.
+//
+// Compared with staging the slices through shared memory, every input word is loaded once per lane and slice
+// rather than once per tap pair, windows are built once per input column rather than once per pair, and the
+// warps of a CTA never wait for each other inside a product: a warp takes 32 consecutive items (a task) and
+// sweeps them alone.  Neighbouring lanes and neighbouring warps read the same input columns at about the same
+// slice, so the repeated reads are served by L1.
+#pragma once
+#include <cstdint>
+#include "qfs_common.cuh"
+
+namespace qfs {
+
+// Half-chunk items of a degree-m form: column s has half_chunks_of(s) items; half_prefix(s) items precede
+// column s.  For s = 8a + b: half_prefix(s) = sum_{s' < s} (s'/8 + 1) = (a + 1)(4a + b).
+__host__ __device__ constexpr int half_chunks_of(int s) { return (s >> 3) + 1; }
+__host__ __device__ constexpr int half_prefix(int s) { return ((s >> 3) + 1) * (4 * (s >> 3) + (s & 7)); }
+
+// Item index i -> (column s, half-chunk h).  Columns 8a .. 8a+7 hold a+1 items each, starting at 4a(a+1).
+__device__ __forceinline__ void decode_half(int i, int &s, int &h) {
+  int a = (int)((sqrtf(1.0f + (float)i) - 1.0f) * 0.5f);
+  while (4 * (a + 1) * (a + 2) <= i) ++a;
+  while (a > 0 && 4 * a * (a + 1) > i) --a;
+  const int rem = i - 4 * a * (a + 1);
+  const int b = rem / (a + 1);
+  h = rem - b * (a + 1);
+  s = 8 * a + b;
+}
+
+// Zeroes the task queue of the swept chain; every kernel that runs a chain product calls it once, before its
+// first barrier.
+__device__ __forceinline__ void init_task_queue(Smem &sm) {
+  if (threadIdx.x == 0) {
+    sm.task_next = 0;
+    sm.task_done = 0;
+  }
+}
+
+namespace sweep {
+
+// Per-lane state of one task (fixed while the lane sweeps the slices).
+struct Lane {
+  int s, h;
+  int off[5];      // word offset of input column s - sI, half-chunk h, inside a slice
+  int out_off;     // word offset of the output half-chunk inside a slice
+  uint32_t colok;  // bit sI: the item exists and s - sI >= 0
+  int pad;         // half-chunks of zero padding after this item that this lane writes (0, 1 or 2)
+  bool valid;      // the item exists
+};
+
+// Input words of slice v for one lane: X[sI] = {word 2h-1, word 2h, word 2h+1} of column s - sI.  The padded
+// layout makes every such read safe and exact without predication: the column (sized for s - sI + 4 entries) holds
+// words 2h .. 2h+1, the word before a column is padding, and a column that does not exist in slice v (s - sI > v,
+// s - sI < 0, or no item) is read from the zero guard words in[-3 .. -1] in front of the buffer.
+template <int P>
+__device__ __forceinline__ void load_slice(const uint32_t *__restrict__ in, const Smem &sm, const Lane &L, int v,
+                                           uint32_t (&X)[5][3]) {
+  const int base = sm.SW[v];
+#pragma unroll
+  for (int sI = 0; sI < 5; ++sI) {
+    const bool ex = ((L.colok >> sI) & 1u) && (L.s - sI <= v);
+    const uint32_t *q = in + (ex ? base + L.off[sI] : -2);
+    const uint2 w = *reinterpret_cast<const uint2 *>(q);
+    X[sI][0] = q[-1];
+    X[sI][1] = w.x;
+    X[sI][2] = w.y;
+  }
+}
+
+// Contributions of input column s - SI of slice v (words X) to the output sets J + uI (mod 5), uI = SI .. 4.
+template <int J, int SI, int FORM, bool DENSE>
+__device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32_t (&tw)[15], uint32_t a44,
+                                            const int (&taps)[35], uint32_t mask, uint32_t colmask,
+                                            int (&acc)[5][8]) {
+  if (!DENSE && !((colmask >> SI) & 1u)) return;  // every tap pair of this input column is zero
+  if (FORM == 1) {
+    // window of output t = 8h + 4q + r: bytes in(t-3 .. t) = bytes r+1 .. r+4 of (word q-1 of the half-chunk,
+    // word q); word -1 is X[0]
+    uint32_t W[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      W[q][0] = __byte_perm(X[q], X[q + 1], 0x4321u);
+      W[q][1] = __byte_perm(X[q], X[q + 1], 0x5432u);
+      W[q][2] = __byte_perm(X[q], X[q + 1], 0x6543u);
+      W[q][3] = X[q + 1];
+    }
+#pragma unroll
+    for (int uI = SI; uI < 5; ++uI) {
+      const int pi = uI * (uI + 1) / 2 + SI;
+      if (DENSE || ((mask >> pi) & 1u)) {
+        const int set = (J + uI) % 5;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            acc[set][4 * q + r] = (int)__dp4a(W[q][r], tw[pi], (unsigned)acc[set][4 * q + r]);
+      }
+    }
+    if (SI == 4 && (DENSE || ((mask >> 14) & 1u))) {
+      // tap (4, 4, 4) reads in(t - 4) = byte r of word q-1
+      const int set = (J + 4) % 5;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          acc[set][4 * q + r] = (int)__dp4a(X[q], a44 << (8 * r), (unsigned)acc[set][4 * q + r]);
+    }
+  } else {
+    // int32 form: b[k] = in(8h - 4 + k), k = 0 .. 11
+    int b[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[k] = (int)((X[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+#pragma unroll
+    for (int uI = SI; uI < 5; ++uI) {
+      const int pi = uI * (uI + 1) / 2 + SI;
+      if (DENSE || ((mask >> pi) & 1u)) {
+        const int set = (J + uI) % 5;
+#pragma unroll
+        for (int tI = 0; tI <= SI; ++tI) {
+          const int a = taps[tet(uI) + tri(SI) + tI];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[set][j] += a * b[j + 4 - tI];
+        }
+      }
+    }
+  }
+}
+
+// Output slice u of this lane is complete in set J: reduce mod p^2 (and, in the last product, apply the Delta_1
+// epilogue), store, and clear the set.
+template <int P, int J, bool LAST, bool DEBUG>
+__device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem &sm, const Lane &L, int u,
+                                         const uint8_t *gs, int (&acc)[5][8], bool &bad, DebugPtrs dbg) {
+  using Pr = Prime<P>;
+  if (L.valid && u >= L.s) {
+    uint32_t w[2] = {0u, 0u}, gw[2] = {0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int G = acc[J][j] % Pr::p2;  // acc >= 0; outputs past the column's end are zero
+      if (LAST) {
+        const int t = 8 * L.h + j;
+        if (DEBUG) gw[j >> 2] |= (uint32_t)G << (8 * (j & 3));
+        if (t <= L.s && (u % P) == 0 && (L.s % P) == 0 && (t % P) == 0) {
+          G -= sm.powp[gs[tet(u / P) + tri(L.s / P) + t / P]];
+          if (G < 0) G += Pr::p2;
+        }
+        if (G % P) bad = true;
+        G /= P;
+      }
+      w[j >> 2] |= (uint32_t)G << (8 * (j & 3));
+    }
+    const int o = sm.SW[u] + L.out_off;
+    if (L.pad == 1) {
+      *reinterpret_cast<uint4 *>(out + o) = make_uint4(w[0], w[1], 0u, 0u);
+      if (DEBUG && LAST) *reinterpret_cast<uint4 *>(dbg.G + o) = make_uint4(gw[0], gw[1], 0u, 0u);
+    } else {
+      *reinterpret_cast<uint2 *>(out + o) = make_uint2(w[0], w[1]);
+      if (DEBUG && LAST) *reinterpret_cast<uint2 *>(dbg.G + o) = make_uint2(gw[0], gw[1]);
+      if (L.pad == 2) {
+        *reinterpret_cast<uint4 *>(out + o + 2) = make_uint4(0u, 0u, 0u, 0u);
+        if (DEBUG && LAST) *reinterpret_cast<uint4 *>(dbg.G + o + 2) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[J][j] = 0;
+}
+
+// One slice step with v = J (mod 5): load slice v, add it to the output sets, finalize output v.
+template <int P, int J, int FORM, bool DENSE, bool LAST, bool DEBUG>
+__device__ __forceinline__ void step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, const Smem &sm,
+                                     const Lane &L, int v, const uint8_t *gs, const uint32_t (&tw)[15], uint32_t a44,
+                                     const int (&taps)[35], uint32_t mask, uint32_t colmask, int (&acc)[5][8],
+                                     bool &bad, DebugPtrs dbg) {
+  uint32_t X[5][3];
+  load_slice<P>(in, sm, L, v, X);
+  column_macs<J, 0, FORM, DENSE>(X[0], tw, a44, taps, mask, colmask, acc);
+  column_macs<J, 1, FORM, DENSE>(X[1], tw, a44, taps, mask, colmask, acc);
+  column_macs<J, 2, FORM, DENSE>(X[2], tw, a44, taps, mask, colmask, acc);
+  column_macs<J, 3, FORM, DENSE>(X[3], tw, a44, taps, mask, colmask, acc);
+  column_macs<J, 4, FORM, DENSE>(X[4], tw, a44, taps, mask, colmask, acc);
+  finalize<P, J, LAST, DEBUG>(out, sm, L, v, gs, acc, bad, dbg);
+}
+
+// Next task of the current product for this warp (warp-uniform), or -1 when the queue is empty.  Tasks are handed
+// out in index order, which is longest first (a task of low columns sweeps more slices).  The last warp to find
+// the queue empty resets it for the next product; the caller's barrier orders that reset before the next product.
+__device__ __forceinline__ int next_task(Smem &sm, int n_tasks) {
+  const int lane = threadIdx.x & 31;
+  int t = 0;
+  if (lane == 0) {
+    t = atomicAdd(&sm.task_next, 1);
+    if (t >= n_tasks && atomicAdd(&sm.task_done, 1) == (int)(blockDim.x >> 5) - 1) {
+      sm.task_next = 0;
+      sm.task_done = 0;
+    }
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  return t < n_tasks ? t : -1;
+}
+
+template <int P, int FORM, bool DENSE, bool LAST, bool DEBUG>
+__device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
+                                       Smem &sm, const uint8_t *gs, uint32_t *status, DebugPtrs dbg) {
+  const int m_out = m_in + 4;
+  const int n_items = half_prefix(m_out + 1);
+  const int n_tasks = (n_items + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = sm.pair_mask;
+  uint32_t colmask = 0;  // bit sI: some pair (uI >= sI, sI) has a nonzero tap
+#pragma unroll
+  for (int sI = 0; sI < 5; ++sI)
+#pragma unroll
+    for (int uI = sI; uI < 5; ++uI)
+      if ((mask >> (uI * (uI + 1) / 2 + sI)) & 1u) colmask |= 1u << sI;
+  uint32_t tw[15];
+  int taps[35];
+  uint32_t a44 = 0;
+  if (FORM == 1) {
+#pragma unroll
+    for (int k = 0; k < 15; ++k) tw[k] = sm.tapword[k];
+    a44 = (uint32_t)sm.taps[34];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 35; ++k) taps[k] = sm.taps[k];
+  }
+  bool bad = false;
+  for (int task = next_task(sm, n_tasks); task >= 0; task = next_task(sm, n_tasks)) {
+    Lane L;
+    const int i = task * 32 + lane;
+    L.valid = i < n_items;
+    decode_half(L.valid ? i : n_items - 1, L.s, L.h);
+    const int s_first = __shfl_sync(0xffffffffu, L.s, 0);
+    L.colok = 0;
+#pragma unroll
+    for (int sI = 0; sI < 5; ++sI) {
+      const int sc = L.s - sI;
+      if (L.valid && sc >= 0) L.colok |= 1u << sI;
+      L.off[sI] = colw(max(sc, 0)) + 2 * L.h;
+    }
+    L.out_off = colw(L.s) + 2 * L.h;
+    // the last item of column s also clears the padding half-chunks after it (2 chunks_of(s) - (s/8 + 1) of them)
+    L.pad = L.h == half_chunks_of(L.s) - 1 ? 2 * chunks_of(L.s) - half_chunks_of(L.s) : 0;
+    int acc[5][8];
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[a][j] = 0;
+    const int v0 = max(0, s_first - 4);
+    int v = v0;
+    int ph = v0 % 5;
+    // slices v0 .. m_in, entering the five-way unrolled loop at phase v0 mod 5
+    while (v <= m_in) {
+      switch (ph) {
+        case 0:
+          step<P, 0, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+          if (++v > m_in) break;
+          [[fallthrough]];
+        case 1:
+          step<P, 1, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+          if (++v > m_in) break;
+          [[fallthrough]];
+        case 2:
+          step<P, 2, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+          if (++v > m_in) break;
+          [[fallthrough]];
+        case 3:
+          step<P, 3, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+          if (++v > m_in) break;
+          [[fallthrough]];
+        default:
+          step<P, 4, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+          ++v;
+      }
+      ph = 0;
+    }
+    // output slices m_in+1 .. m_out take no further input
+    for (int u = m_in + 1; u <= m_out; ++u) {
+      switch (u % 5) {
+        case 0: finalize<P, 0, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
+        case 1: finalize<P, 1, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
+        case 2: finalize<P, 2, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
+        case 3: finalize<P, 3, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
+        default: finalize<P, 4, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
+      }
+    }
+  }
+  if (bad) atomicOr(status, kStatusInexactDivision);
+}
+
+}  // namespace sweep
+
+// Entry point used by chain_step for the dp4a (FORM 1) and int32 (FORM 0) forms.  Quartics with few zero tap
+// pairs run every pair; the others skip zero pairs (and input columns none of whose pairs is nonzero).
+// The caller runs it with every warp of the CTA, between two barriers, with sm.task_next and sm.task_done zero
+// (init_task_queue at kernel start; run_tasks leaves them zero).
+template <int P, int FORM, bool LAST, bool DEBUG>
+__device__ __forceinline__ void sweep_chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                 int m_in, Smem &sm, const uint8_t *gs, uint32_t *status,
+                                                 DebugPtrs dbg) {
+  if (__popc(sm.pair_mask) >= 12)
+    sweep::run_tasks<P, FORM, true, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);
+  else
+    sweep::run_tasks<P, FORM, false, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);
+}
+
+}  // namespace qfs

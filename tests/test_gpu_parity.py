@@ -243,6 +243,7 @@ def test_staged_engine_matches_fused_and_oracle(qfs, p, n):
     for max_h in (1, 3):
         assert np.array_equal(qfs.heights(p, t, engine="staged", max_h=max_h).cpu().numpy(),
                               qfs.heights(p, t, max_h=max_h).cpu().numpy())
+    assert qfs.read_status() == 0
 
 
 def test_staged_engine_small_chunks_and_multi(qfs):
@@ -253,6 +254,7 @@ def test_staged_engine_small_chunks_and_multi(qfs):
     outs = qfs.heights_multi([(5, t5, None), (7, t7, None)], engine="staged", workspace_budget=64 << 20)
     assert np.array_equal(outs[0].cpu().numpy(), oracle.heights(5, f5))
     assert np.array_equal(outs[1].cpu().numpy(), oracle.heights(7, f7))
+    assert qfs.read_status() == 0
 
 
 # ------------------------------------------------------------------------------------- identity power mode
