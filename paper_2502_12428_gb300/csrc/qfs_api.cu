@@ -154,19 +154,20 @@ int run_staged(DeviceState &S, const FusedParams &prm, const qfs_options_t *opts
   return QFS_OK;
 }
 
-cudaError_t form_occupancy(int form, int *blocks, size_t smem) {
+// small: every group of the launch has p <= 5 (the small-prime kernel, three CTAs per SM)
+cudaError_t form_occupancy(int form, int *blocks, size_t smem, bool small) {
   switch (form) {
-    case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem);
-    case QFS_FORM_INT8TC: return FormLauncher<2>::occupancy(blocks, smem);
-    default: return FormLauncher<1>::occupancy(blocks, smem);
+    case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem, small);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::occupancy(blocks, smem, small);
+    default: return FormLauncher<1>::occupancy(blocks, smem, small);
   }
 }
 
-cudaError_t form_fused(int form, const FusedParams &prm, int grid, size_t smem, cudaStream_t st) {
+cudaError_t form_fused(int form, const FusedParams &prm, int grid, size_t smem, cudaStream_t st, bool small) {
   switch (form) {
-    case QFS_FORM_INT32: return FormLauncher<0>::fused(prm, grid, smem, st);
-    case QFS_FORM_INT8TC: return FormLauncher<2>::fused(prm, grid, smem, st);
-    default: return FormLauncher<1>::fused(prm, grid, smem, st);
+    case QFS_FORM_INT32: return FormLauncher<0>::fused(prm, grid, smem, st, small);
+    case QFS_FORM_INT8TC: return FormLauncher<2>::fused(prm, grid, smem, st, small);
+    default: return FormLauncher<1>::fused(prm, grid, smem, st, small);
   }
 }
 
@@ -195,7 +196,7 @@ int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_op
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
   if (per_sm == 0) {
     int blocks = 0;
-    cudaError_t e = form_occupancy(form, &blocks, plan.smem);
+    cudaError_t e = form_occupancy(form, &blocks, plan.smem, max_p <= 5);
     if (e != cudaSuccess) return cuda_fail(e);
     per_sm = std::max(1, blocks);
   }
@@ -301,7 +302,8 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   // shared memory: the largest iterate pair of the launch plus the largest ring any group's tile needs
   int ring_words = 0;
   for (int i = 0; i < prm.n_groups; ++i)
-    ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p), form == QFS_FORM_INT8TC));
+    ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p),
+                                                     uses_ring_chain(form, prm.g[i].p)));
   const size_t smem = ring_offset_for(tet(4 * (max_p - 1) + 1)) + 4 * (size_t)ring_words;
   Plan plan;
   rc = make_plan(*S, form, max_p, n_items, opts, plan, smem);
@@ -313,7 +315,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   prm.ws_words = plan.ws_words;
   cudaError_t e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = form_fused(form, prm, plan.grid, plan.smem, stream);
+  e = form_fused(form, prm, plan.grid, plan.smem, stream, max_p <= 5);
   if (e != cudaSuccess) return cuda_fail(e);
   return QFS_OK;
 }
@@ -340,7 +342,7 @@ int qfs_plan_prepare(int p, int64_t n_hint) {
   Plan plan;
   int64_t n = n_hint > 0 ? n_hint : (int64_t)1 << 40;
   for (int form : {QFS_FORM_INT32, QFS_FORM_DP4A, QFS_FORM_INT8TC}) {
-    rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p), form == QFS_FORM_INT8TC));
+    rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p), uses_ring_chain(form, p)));
     if (rc) return rc;
   }
   cudaError_t e = cudaDeviceSynchronize();

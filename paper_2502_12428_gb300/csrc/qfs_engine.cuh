@@ -102,9 +102,13 @@ __host__ __device__ inline int aux_ring_words(int p, TileConfig tc, bool ring_ch
   return max(ring_off + chain, (l_fpm2 + l_d1f + l_E + 3) / 4);
 }
 
-// Shared-memory ring words for prime p: the chain's slice ring (only the int8 tensor form stages slices in shared
-// memory; the dp4a and int32 forms sweep them from global memory), theta's Delta slots, and the power modes'
-// arrays.  ring_chain = true gives the size every form fits in.
+// Which chain product a form runs at prime p: the shared-memory slice ring (the int8 tensor form, and every form
+// at p <= 5, where the forms are small enough that staging their slices pays), or the lane sweep over global
+// memory (dp4a and int32 forms at p >= 7).
+__host__ __device__ constexpr bool uses_ring_chain(int form, int p) { return form == 2 || p <= 5; }
+
+// Shared-memory ring words for prime p: the chain's slice ring (when the chain stages slices in shared memory),
+// theta's Delta slots, and the power modes' arrays.  ring_chain = true gives the size every form fits in.
 __host__ __device__ inline int ring_words_for(int p, TileConfig tc, bool ring_chain = true) {
   return max(max(ring_chain ? chain_slot_words(p, tc) : 0, theta_ring_words_for(p)), aux_ring_words(p, tc, ring_chain));
 }
@@ -442,13 +446,13 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
   if (bad) atomicOr(status, kStatusInexactDivision);
 }
 
-// One product of the chain.  The dp4a and int32 forms sweep the input slices lane by lane (qfs_sweep.cuh); the
-// int8 tensor form runs its tiles over the shared-memory slice ring above.
+// One product of the chain: over the shared-memory slice ring above (int8 tensor form; every form at p <= 5), or
+// lane by lane over the input slices in global memory (qfs_sweep.cuh; dp4a and int32 forms at p >= 7).
 template <int P, int FORM, bool LAST, bool DEBUG>
 __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
                                            Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
                                            DebugPtrs dbg) {
-  if constexpr (FORM == 2)
+  if constexpr (uses_ring_chain(FORM, P))
     ring_chain_step<P, FORM, LAST, DEBUG>(in, out, m_in, sm, ring, gs, status, dbg);
   else
     sweep_chain_step<P, FORM, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);
@@ -1199,7 +1203,9 @@ struct FusedParams {
   int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut, 2: reduced theta
 };
 
-template <int FORM>
+// SMALL: a launch whose primes are all <= 5 (every group runs the shared-memory ring chain); the kernel then needs
+// no code for larger primes and can keep three CTAs per SM.
+template <int FORM, bool SMALL>
 __device__ __forceinline__ void fused_body(const FusedParams &prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -1233,9 +1239,17 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
     switch (G.p) {
       case 3: h = process_quartic<3, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
       case 5: h = process_quartic<5, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
-      case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
-      case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
-      default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+      default:
+        if constexpr (SMALL) {
+          h = -1;   // not reached: the host launches the small-prime kernel only when every group has p <= 5
+        } else {
+          switch (G.p) {
+            case 7: h = process_quartic<7, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+            case 11: h = process_quartic<11, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+            default: h = process_quartic<13, FORM, false>(f, prm.max_h, sm, gs, gn, ring, bufA, bufB, prm.status, dbg, steps, prm.power_mode); break;
+          }
+        }
+        break;
     }
     if (threadIdx.x == 0) {
       G.heights[row] = (int8_t)h;

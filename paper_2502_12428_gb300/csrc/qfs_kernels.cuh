@@ -12,7 +12,12 @@ constexpr int min_ctas_per_sm() { return FORM == 2 ? 3 : 2; }
 // Persistent launch: every CTA pulls quartics from a global atomic queue until the queue is empty.
 template <int FORM>
 __global__ void __launch_bounds__(kThreads, min_ctas_per_sm<FORM>()) fused_kernel(FusedParams prm) {
-  fused_body<FORM>(prm);
+  fused_body<FORM, false>(prm);
+}
+// The same for launches whose primes are all <= 5 (ring chain only): 85 registers, three CTAs per SM.
+template <int FORM>
+__global__ void __launch_bounds__(kThreads, 3) fused_kernel_small(FusedParams prm) {
+  fused_body<FORM, true>(prm);
 }
 
 // One quartic with every intermediate array written out (kernel-level parity hook).
@@ -40,8 +45,8 @@ __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int m
 // Host-side launchers (defined in qfs_form_<name>.cu).
 template <int FORM>
 struct FormLauncher {
-  static cudaError_t fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st);
-  static cudaError_t occupancy(int *blocks_per_sm, size_t smem);
+  static cudaError_t fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st, bool small);
+  static cudaError_t occupancy(int *blocks_per_sm, size_t smem, bool small);
   static cudaError_t debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA, uint32_t *bufB,
                            uint32_t *status, DebugPtrs dbg, cudaStream_t st, int power_mode);
 };
@@ -52,19 +57,20 @@ struct FormLauncher {
 
 #define QFS_DEFINE_FORM_LAUNCHER(FORM)                                                                        \
   template <>                                                                                                 \
-  cudaError_t FormLauncher<FORM>::fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st) {     \
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                         (int)smem);                                                          \
+  cudaError_t FormLauncher<FORM>::fused(const FusedParams &prm, int grid, size_t smem, cudaStream_t st,      \
+                                        bool small) {                                                         \
+    auto k = small ? fused_kernel_small<FORM> : fused_kernel<FORM>;                                           \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
     if (e != cudaSuccess) return e;                                                                           \
-    fused_kernel<FORM><<<grid, kThreads, smem, st>>>(prm);                                                    \
+    k<<<grid, kThreads, smem, st>>>(prm);                                                                     \
     return cudaGetLastError();                                                                                \
   }                                                                                                           \
   template <>                                                                                                 \
-  cudaError_t FormLauncher<FORM>::occupancy(int *blocks_per_sm, size_t smem) {                                \
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                         (int)smem);                                                          \
+  cudaError_t FormLauncher<FORM>::occupancy(int *blocks_per_sm, size_t smem, bool small) {                    \
+    auto k = small ? fused_kernel_small<FORM> : fused_kernel<FORM>;                                           \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
     if (e != cudaSuccess) return e;                                                                           \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<FORM>, kThreads, smem);  \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);                   \
   }
 
 #define QFS_DEFINE_DEBUG_LAUNCHER(FORM)                                                                       \
@@ -72,7 +78,7 @@ struct FormLauncher {
   cudaError_t FormLauncher<FORM>::debug(int p, const uint8_t *f, int max_h, int8_t *h_out, uint32_t *bufA,    \
                                         uint32_t *bufB, uint32_t *status, DebugPtrs dbg, cudaStream_t st,     \
                                         int power_mode) {                                                     \
-    const size_t smem = smem_bytes_for(p, FORM == 2);                                                         \
+    const size_t smem = smem_bytes_for(p, uses_ring_chain(FORM, p));                                         \
     cudaError_t e = cudaSuccess;                                                                              \
     switch (p) {                                                                                              \
       case 3: QFS_DEBUG_LAUNCH(3, FORM); break;                                                               \

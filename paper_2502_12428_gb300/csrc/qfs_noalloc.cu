@@ -26,7 +26,7 @@ constexpr size_t kControlBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // The fused persistent kernel (dp4a form), given its workspace in the fixed array instead of a cudaMalloc'd one.
-__global__ void __launch_bounds__(kThreads, 2) noalloc_fused_kernel(FusedParams prm) { fused_body<1>(prm); }
+__global__ void __launch_bounds__(kThreads, 2) noalloc_fused_kernel(FusedParams prm) { fused_body<1, false>(prm); }
 
 constexpr int kMaxDev = 64;
 void *g_scratch_addr[kMaxDev];   // device address of g_noalloc_scratch on each device, set once
@@ -80,7 +80,7 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   int rc = scratch_for_current_device(&scratch, &sms);
   if (rc) return rc;
 
-  const size_t smem = smem_bytes_for(p, /*ring_chain=*/false);
+  const size_t smem = smem_bytes_for(p, uses_ring_chain(QFS_FORM_DP4A, p));
   cudaError_t e = cudaFuncSetAttribute(noalloc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return QFS_ERR_CUDA;

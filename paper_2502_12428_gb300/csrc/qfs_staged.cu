@@ -223,7 +223,7 @@ template <int P>
 cudaError_t run_chunks(const StagedPlan &pl, const uint8_t *coeffs, int8_t *heights, int64_t n, int max_h,
                        cudaStream_t st) {
   using Pr = Prime<P>;
-  const size_t smem = smem_bytes_for(P, /*ring_chain=*/false);
+  const size_t smem = smem_bytes_for(P, uses_ring_chain(QFS_FORM_DP4A, P));
   cudaError_t e;
   for (auto k : {(const void *)stage_fedder<P>, (const void *)stage_power<P>, (const void *)stage_theta<P>}) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -281,7 +281,7 @@ cudaError_t staged_run(const StagedPlan &pl, int p, const uint8_t *coeffs, int8_
 }
 
 cudaError_t staged_occupancy(int p, int *blocks) {
-  const size_t smem = smem_bytes_for(p, /*ring_chain=*/false);
+  const size_t smem = smem_bytes_for(p, uses_ring_chain(QFS_FORM_DP4A, p));
   const void *k = p == 3 ? (const void *)stage_power<3> : p == 5 ? (const void *)stage_power<5>
                 : p == 7 ? (const void *)stage_power<7> : p == 11 ? (const void *)stage_power<11>
                 : (const void *)stage_power<13>;
