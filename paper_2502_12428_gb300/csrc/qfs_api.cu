@@ -154,7 +154,7 @@ int run_staged(DeviceState &S, const FusedParams &prm, const qfs_options_t *opts
   return QFS_OK;
 }
 
-// small: every group of the launch has p <= 5 (the small-prime kernel, three CTAs per SM)
+// small: an int8 tensor form launch whose groups all have p <= 5 (the small-prime kernel, three CTAs per SM)
 cudaError_t form_occupancy(int form, int *blocks, size_t smem, bool small) {
   switch (form) {
     case QFS_FORM_INT32: return FormLauncher<0>::occupancy(blocks, smem, small);
@@ -196,7 +196,7 @@ int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_op
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
   if (per_sm == 0) {
     int blocks = 0;
-    cudaError_t e = form_occupancy(form, &blocks, plan.smem, max_p <= 5);
+    cudaError_t e = form_occupancy(form, &blocks, plan.smem, form == QFS_FORM_INT8TC && max_p <= 5);
     if (e != cudaSuccess) return cuda_fail(e);
     per_sm = std::max(1, blocks);
   }
@@ -315,7 +315,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   prm.ws_words = plan.ws_words;
   cudaError_t e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = form_fused(form, prm, plan.grid, plan.smem, stream, max_p <= 5);
+  e = form_fused(form, prm, plan.grid, plan.smem, stream, form == QFS_FORM_INT8TC && max_p <= 5);
   if (e != cudaSuccess) return cuda_fail(e);
   return QFS_OK;
 }

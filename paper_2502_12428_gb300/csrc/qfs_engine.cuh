@@ -102,10 +102,9 @@ __host__ __device__ inline int aux_ring_words(int p, TileConfig tc, bool ring_ch
   return max(ring_off + chain, (l_fpm2 + l_d1f + l_E + 3) / 4);
 }
 
-// Which chain product a form runs at prime p: the shared-memory slice ring (the int8 tensor form, and every form
-// at p <= 5, where the forms are small enough that staging their slices pays), or the lane sweep over global
-// memory (dp4a and int32 forms at p >= 7).
-__host__ __device__ constexpr bool uses_ring_chain(int form, int p) { return form == 2 || p <= 5; }
+// Which chain product a form runs at prime p: the shared-memory slice ring (the int8 tensor form, whose tiles read
+// aligned words of a staged slice), or the lane sweep over global memory (dp4a and int32 forms).
+__host__ __device__ constexpr bool uses_ring_chain(int form, int p) { return form == 2 && p > 0; }
 
 // Shared-memory ring words for prime p: the chain's slice ring (when the chain stages slices in shared memory),
 // theta's Delta slots, and the power modes' arrays.  ring_chain = true gives the size every form fits in.
@@ -446,8 +445,8 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
   if (bad) atomicOr(status, kStatusInexactDivision);
 }
 
-// One product of the chain: over the shared-memory slice ring above (int8 tensor form; every form at p <= 5), or
-// lane by lane over the input slices in global memory (qfs_sweep.cuh; dp4a and int32 forms at p >= 7).
+// One product of the chain: over the shared-memory slice ring above (int8 tensor form), or lane by lane over the
+// input slices in global memory (qfs_sweep.cuh; dp4a and int32 forms).
 template <int P, int FORM, bool LAST, bool DEBUG>
 __device__ __forceinline__ void chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int m_in,
                                            Smem &sm, uint32_t *ring, const uint8_t *gs, uint32_t *status,
@@ -1203,8 +1202,8 @@ struct FusedParams {
   int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut, 2: reduced theta
 };
 
-// SMALL: a launch whose primes are all <= 5 (every group runs the shared-memory ring chain); the kernel then needs
-// no code for larger primes and can keep three CTAs per SM.
+// SMALL: an int8 tensor form launch whose primes are all <= 5; the kernel then needs no code for larger primes and
+// can keep three CTAs per SM.
 template <int FORM, bool SMALL>
 __device__ __forceinline__ void fused_body(const FusedParams &prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

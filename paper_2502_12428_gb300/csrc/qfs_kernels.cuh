@@ -14,7 +14,7 @@ template <int FORM>
 __global__ void __launch_bounds__(kThreads, min_ctas_per_sm<FORM>()) fused_kernel(FusedParams prm) {
   fused_body<FORM, false>(prm);
 }
-// The same for launches whose primes are all <= 5 (ring chain only): 85 registers, three CTAs per SM.
+// The same for int8 tensor form launches whose primes are all <= 5: 85 registers, three CTAs per SM.
 template <int FORM>
 __global__ void __launch_bounds__(kThreads, 3) fused_kernel_small(FusedParams prm) {
   fused_body<FORM, true>(prm);

@@ -7,8 +7,8 @@
 // input slices v upwards.  Input slice v feeds output slices u = v .. v+4 (tap pairs uI = u - v): the lane loads
 // the five input columns s - sI (sI = 0..4) of slice v once (eight bytes plus the word before them), builds the
 // byte windows once, and adds every tap pair (uI, sI) with uI >= sI into the accumulator set of output u = v + uI.
-// Five accumulator sets rotate with v mod 5 (the loop is unrolled five ways so that every index is static); after
-// slice v the set of output v is complete and is reduced, packed and stored.
+// Five accumulator sets, set k holding output slice v + k; after slice v, set 0 (output v) is complete and is
+// reduced, packed and stored, and the sets move down one place.
 //
 // Compared with staging the slices through shared memory, every input word is loaded once per lane and slice
 // rather than once per tap pair, windows are built once per input column rather than once per pair, and the
@@ -257,43 +257,22 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[a][j] = 0;
     const int v0 = max(0, s_first - 4);
-    int v = v0;
-    int ph = v0 % 5;
-    // slices v0 .. m_in, entering the five-way unrolled loop at phase v0 mod 5
-    while (v <= m_in) {
-      switch (ph) {
-        case 0:
-          step<P, 0, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
-          if (++v > m_in) break;
-          [[fallthrough]];
-        case 1:
-          step<P, 1, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
-          if (++v > m_in) break;
-          [[fallthrough]];
-        case 2:
-          step<P, 2, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
-          if (++v > m_in) break;
-          [[fallthrough]];
-        case 3:
-          step<P, 3, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
-          if (++v > m_in) break;
-          [[fallthrough]];
-        default:
-          step<P, 4, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
-          ++v;
-      }
-      ph = 0;
+    // slices v0 .. m_in; after each slice the accumulator sets move down one place (set 0 always holds the output
+    // slice that the current input slice completes), so one copy of the step serves every slice
+    for (int v = v0; v <= m_in; ++v) {
+      step<P, 0, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[a][j] = acc[a + 1][j];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[4][j] = 0;
     }
-    // output slices m_in+1 .. m_out take no further input
-    for (int u = m_in + 1; u <= m_out; ++u) {
-      switch (u % 5) {
-        case 0: finalize<P, 0, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
-        case 1: finalize<P, 1, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
-        case 2: finalize<P, 2, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
-        case 3: finalize<P, 3, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
-        default: finalize<P, 4, LAST, DEBUG>(out, sm, L, u, gs, acc, bad, dbg); break;
-      }
-    }
+    // output slices m_in+1 .. m_out take no further input: they sit in sets 0 .. 3
+    finalize<P, 0, LAST, DEBUG>(out, sm, L, m_in + 1, gs, acc, bad, dbg);
+    finalize<P, 1, LAST, DEBUG>(out, sm, L, m_in + 2, gs, acc, bad, dbg);
+    finalize<P, 2, LAST, DEBUG>(out, sm, L, m_in + 3, gs, acc, bad, dbg);
+    finalize<P, 3, LAST, DEBUG>(out, sm, L, m_in + 4, gs, acc, bad, dbg);
   }
   if (bad) atomicOr(status, kStatusInexactDivision);
 }
