@@ -323,6 +323,23 @@ def run_ours(args):
             "value": round(world * n / (max_over_ranks(statistics.mean(per_s)) / 1e3), 1),
             "ms_per_step": round(max_over_ranks(statistics.mean(per_s)), 3),
             "bit_exact_vs_fused": bool(np.array_equal(os_.cpu().numpy(), heights_np))}
+        # theta-matrix export (Sec. 3.4's M, every quartic): the first 2 x SMs quartics of the headline workload
+        nm = 2 * torch.cuda.get_device_properties(dev).multi_processor_count
+        sub = coeffs[:nm].contiguous()
+        ld = (4 * p - 1) * (4 * p - 2) * (4 * p - 3) // 6
+        mbuf = torch.empty(nm, ld, ld, dtype=torch.uint8, device=dev)
+        qfs.theta_matrix(p, sub, out=mbuf)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qfs.theta_matrix(p, sub, out=mbuf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msm = max_over_ranks(e0.elapsed_time(e1))
+        extra[workload_name(HEADLINE_CFG) + " theta-matrix export"] = {
+            "value": round(world * nm / (msm / 1e3), 1), "unit": "matrices/s", "ms": round(msm, 3),
+            "quartics": nm, "matrix_bytes": ld * ld}
+        del mbuf
 
     # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step
     host_in = torch.from_numpy(f_np).pin_memory()

@@ -176,6 +176,18 @@ int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int max_h, int8
 int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t *g_out, int32_t *G_out,
                      int32_t *delta_out, int32_t *iters_out, int8_t *height_out);
 
+/* The theta matrix of each of n quartics (the matrix form of the step of Algorithm 3, Sec. 3.4):
+     M[r][c] = Delta_1(f^(p-1))[p r + (p-1,p-1,p-1,p-1) - c]  (mod p),  r, c in B_d (d = 4(p-1), descending lex),
+   and 0 where that exponent falls outside the degree-4p(p-1) monomials, so that theta(g) = M g (mod p) for every
+   form g of degree d.  The height pipeline never forms M; this exports it.  Unlike qfs_heights, the Fedder test
+   does not stop the computation: M is produced for every quartic.
+   coeffs: device, n x 35 uint8, row-major, descending lex, values in [0, p).  M_out: device, n x ld x ld uint8
+   (ld = C(4p-1, 3): 2925 at p = 7, 12341 at p = 11), row-major; caller-owned.  A row of coeffs with a value >= p
+   gives an all-zero M.  Stream-ordered; may grow the library workspace (cudaMalloc) on the first call for p.
+   Returns QFS_OK or an error status (QFS_ERR_INVALID_P, QFS_ERR_INVALID_N, QFS_ERR_NULL, QFS_ERR_NO_MEMORY,
+   QFS_ERR_CUDA). */
+int qfs_theta_matrix(int p, int64_t n, const uint8_t *coeffs, uint8_t *M_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

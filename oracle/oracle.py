@@ -21,7 +21,7 @@ _SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
 _lib = None
 
 __all__ = ["build", "lib", "load", "Oracle", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
-           "stage_arrays_a", "stage_arrays_r", "ROUTE_A", "ROUTE_R"]
+           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "ROUTE_A", "ROUTE_R"]
 
 ROUTE_A = 0
 ROUTE_R = 1
@@ -204,3 +204,36 @@ def split_u(p, P, deg):
     out = np.zeros(monomial_count(rem // p), np.int32)
     d = lib().qfs_oracle_split_u(p, deg, _ptr(P, ctypes.c_int32), _ptr(out, ctypes.c_int32))
     return d, out
+
+
+def theta_matrix(p, f):
+    """The theta matrix of quartic f (Sec. 3.4, the matrix form of Algorithm 3's step), by its definition:
+    M[r][c] = Delta[p r + (p-1)1 - c] for r, c in B_d (descending lex), Delta = Delta_1(g) mod p with g = f^(p-1)
+    mod p (Algorithm 1 via delta1), and 0 where the exponent leaves the degree-4p(p-1) monomials.  Returns a uint8
+    array (ld, ld).  theta(g) = M g mod p; the pins check that against route A's iterates."""
+    f = _quartic(f)
+    d, D = 4 * (p - 1), 4 * p * (p - 1)
+    ld = monomial_count(d)
+    g = np.zeros(ld, np.int32)
+    D_ = np.zeros(monomial_count(D), np.int32)
+    delta = np.zeros(monomial_count(D), np.int32)
+    iters = np.zeros((1, ld), np.int32)
+    lib().qfs_oracle_height_a(p, _ptr(f, ctypes.c_uint8), 1, 0, _ptr(g, ctypes.c_int32), _ptr(D_, ctypes.c_int32),
+                              _ptr(delta, ctypes.c_int32), _ptr(iters, ctypes.c_int32))
+    _, delta = delta1(p, g, d)
+    # exponent vectors (x1..x4) of B_d and of the degree-D monomials, descending lex
+    def monomials(deg):
+        out = []
+        for a in range(deg, -1, -1):
+            for b in range(deg - a, -1, -1):
+                for c in range(deg - a - b, -1, -1):
+                    out.append((a, b, c, deg - a - b - c))
+        return np.array(out, dtype=np.int64)
+    B = monomials(d)
+    index = {tuple(e): i for i, e in enumerate(monomials(D))}
+    M = np.zeros((ld, ld), np.uint8)
+    for r in range(ld):
+        e = p * B[r][None, :] + (p - 1) - B       # exponent of Delta paired with each column c
+        for c in np.nonzero((e >= 0).all(axis=1))[0]:
+            M[r, c] = delta[index[tuple(e[c])]]
+    return M

@@ -11,6 +11,7 @@
 #include "../../include/qfs.h"
 #include "qfs_kernels.cuh"
 #include "qfs_staged.cuh"
+#include "qfs_theta_matrix.cuh"
 
 namespace qfs {
 
@@ -26,6 +27,8 @@ struct DeviceState {
   void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32), [16]: stats (2 x u64)
   void *staged = nullptr;      // staged-engine survivor buffers
   size_t staged_bytes = 0;
+  int *which = nullptr;        // theta-matrix export: which workspace buffer holds each quartic's Delta
+  int which_n = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -361,6 +364,7 @@ int qfs_shutdown(void) {
     if (S.ws && cudaFree(S.ws) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.ctrl && cudaFree(S.ctrl) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.staged && cudaFree(S.staged) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.which && cudaFree(S.which) != cudaSuccess) rc = QFS_ERR_CUDA;
     S = DeviceState();
   }
   cudaSetDevice(cur);
@@ -552,5 +556,42 @@ extern "C" int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int for
   if (iters_out && max_h > 1) cudaMemcpy(iters_out, itmp, ld * 4 * (max_h - 1), cudaMemcpyDeviceToDevice);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
   cudaFree(A); cudaFree(B); cudaFree(Gp); cudaFree(Dp); cudaFree(gtmp); cudaFree(itmp); cudaFree(SWg);
+  return QFS_OK;
+}
+
+extern "C" int qfs_theta_matrix(int p, int64_t n, const uint8_t *coeffs, uint8_t *M_out, cudaStream_t stream) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (n < 0) return QFS_ERR_INVALID_N;
+  if (n > 0 && (!coeffs || !M_out)) return QFS_ERR_NULL;
+  if (n == 0) return QFS_OK;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  const size_t stride = workspace_stride_words(p);
+  const size_t ld = (size_t)tet(4 * (p - 1) + 1);
+  // quartics per batch: one CTA each, bounded by the SM count and by the workspace budget
+  int64_t batch = std::min<int64_t>(n, 2 * (int64_t)S->sms);
+  batch = std::min<int64_t>(batch, (int64_t)(default_budget(*S) / (2 * stride * sizeof(uint32_t))));
+  if (batch < 1) return QFS_ERR_NO_MEMORY;
+  rc = ensure_workspace(*S, workspace_words(batch, stride) * sizeof(uint32_t));
+  if (rc) return rc;
+  if (S->which_n < batch) {
+    if (S->which) cudaFree(S->which);
+    S->which = nullptr;
+    S->which_n = 0;
+    if (cudaMalloc(&S->which, sizeof(int) * (size_t)batch) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return QFS_ERR_NO_MEMORY;
+    }
+    S->which_n = (int)batch;
+  }
+  uint32_t *status = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(S->ctrl) + 8);
+  for (int64_t i0 = 0; i0 < n; i0 += batch) {
+    const int nb = (int)std::min<int64_t>(batch, n - i0);
+    cudaError_t e = theta_matrix_launch(p, coeffs + 35 * i0, nb, M_out + (size_t)i0 * ld * ld,
+                                        static_cast<uint32_t *>(S->ws), stride, S->which, status, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   return QFS_OK;
 }

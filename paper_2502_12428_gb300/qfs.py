@@ -64,6 +64,7 @@ def _lib():
         L.qfs_last_cuda_error.argtypes = []
         L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
         L.qfs_heights_noalloc.argtypes = [c_int, i64, vp, c_int, vp, vp]
+        L.qfs_theta_matrix.argtypes = [c_int, i64, vp, vp, vp]
         L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
         L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -71,7 +72,8 @@ def _lib():
                                    ctypes.POINTER(ctypes.c_float)]
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
-                     "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune"):
+                     "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
+                     "qfs_theta_matrix"):
             getattr(L, name).restype = c_int
         _LIB = L
         load_tile_table()
@@ -172,6 +174,22 @@ def heights_noalloc(p, coeffs, max_h=10, out=None, stream=None):
                                     _stream(stream))
     _check(rc, "qfs_heights_noalloc")
     return out
+
+
+def theta_matrix(p, coeffs, out=None, stream=None):
+    """qfs_theta_matrix: the theta matrix M of each quartic (coeffs: CUDA uint8 (n, 35) or (35,)), as a CUDA uint8
+    tensor (n, ld, ld) or (ld, ld), ld = C(4p-1, 3): M[r][c] = Delta_1(f^(p-1))[p r + (p-1)1 - c] mod p, so that
+    theta(g) = M g mod p."""
+    _need_cuda(coeffs, torch.uint8, "coeffs")
+    single = coeffs.dim() == 1
+    c2 = coeffs.reshape(-1, 35).contiguous()
+    ld = (4 * p - 1) * (4 * p - 2) * (4 * p - 3) // 6
+    if out is None:
+        out = torch.empty(c2.shape[0], ld, ld, dtype=torch.uint8, device=coeffs.device)
+    _need_cuda(out, torch.uint8, "out")
+    rc = _lib().qfs_theta_matrix(int(p), int(c2.shape[0]), c2.data_ptr(), out.data_ptr(), _stream(stream))
+    _check(rc, "qfs_theta_matrix")
+    return out[0] if single else out
 
 
 TILE_TABLE = os.path.join(_HERE, "tile_table.json")

@@ -370,3 +370,31 @@ def test_reduced_mode_paper_examples(qfs):
         f = np.stack([r[3] for r in sel])
         want = np.array([r[1] for r in sel], np.int8)
         assert np.array_equal(qfs.heights(p, dev_tensor(f), power="reduced").cpu().numpy(), want), p
+
+
+# ------------------------------------------------------------------------------------- theta matrix export
+@pytest.mark.parametrize("p,n", [(3, 8), (5, 3), (7, 1)])
+def test_theta_matrix_matches_oracle(qfs, p, n):
+    # every entry of M equals the oracle's M from its definition; height-1 rows are exported too
+    f = np.concatenate([inputs.dense(p, n, 8800 + p), inputs.sparse(p, 1, 8900 + p)])
+    got = qfs.theta_matrix(p, dev_tensor(f)).cpu().numpy()
+    for i in range(len(f)):
+        assert np.array_equal(got[i], oracle.theta_matrix(p, f[i])), i
+    assert qfs.read_status() == 0
+
+
+def test_theta_matrix_applies_theta_and_rejects_bad_rows(qfs):
+    # M g = theta(g): the device's first iterate, and an invalid row gives M = 0
+    p = 5
+    f, h = find_rows(p, 400, 8950, lambda x: x >= 2, 2)
+    bad = f[:1].copy()
+    bad[0, 7] = p
+    rows = np.concatenate([f, bad])
+    M = qfs.theta_matrix(p, dev_tensor(rows)).cpu().numpy().astype(np.int64)
+    for i in range(len(f)):
+        st = qfs.debug_stages(p, dev_tensor(f[i]))
+        g = st["g"].cpu().numpy().astype(np.int64)
+        assert np.array_equal(M[i] @ g % p, st["iters"].cpu().numpy()[0])
+    assert not M[-1].any()
+    with pytest.raises(qfs.QfsError):
+        qfs.theta_matrix(4, dev_tensor(f))

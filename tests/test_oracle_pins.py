@@ -263,3 +263,32 @@ def test_height_statistics_p5():
     sigma = (0.2 * 0.8 / n) ** 0.5
     assert abs(frac - 1 / p) < 5 * sigma
     assert set(np.unique(h)) <= set(range(0, 11))
+
+
+# ------------------------------------------------------------------------------------- theta matrix (Sec. 3.4)
+@pytest.mark.parametrize("p", [3, 5])
+def test_theta_matrix_reproduces_route_a_iterates(p):
+    """The matrix built from its definition (M[r][c] = Delta[p r + (p-1)1 - c]) maps each iterate of route A -- the
+    full product Delta g followed by Algorithm 2's u -- to the next one."""
+    f = inputs.dense(p, 300, 4100 + p)
+    h = oracle.heights(p, f, route=oracle.ROUTE_A)
+    rows = [i for i in range(len(f)) if h[i] >= 3 or h[i] == 0][:3]
+    assert rows
+    for i in rows:
+        ref = oracle.stage_arrays_a(p, f[i])
+        M = oracle.theta_matrix(p, f[i]).astype(np.int64)
+        seq = [ref["g"].astype(np.int64)] + [x.astype(np.int64) for x in ref["iters"]]
+        for a, b in zip(seq, seq[1:]):
+            assert np.array_equal(M @ a % p, b)
+
+
+def test_theta_matrix_shape_and_sparsity():
+    """Entries outside the Delta cone are zero: at p = 3 the nonzero pattern of M covers at most the 60 % of
+    entries whose exponent p r + (p-1)1 - c is nonnegative (nnz of M, 16,245 of 165^2)."""
+    p = 3
+    M = oracle.theta_matrix(p, inputs.dense(p, 1, 4200)[0])
+    assert M.shape == (165, 165) and M.max() < p
+    B = np.array(monomials(4 * (p - 1)))
+    support = sum(int(((p * B[r][None, :] + (p - 1) - B) >= 0).all(axis=1).sum()) for r in range(len(B)))
+    assert support == 16245
+    assert np.count_nonzero(M) <= support
