@@ -340,6 +340,23 @@ def run_ours(args):
             "value": round(world * nm / (msm / 1e3), 1), "unit": "matrices/s", "ms": round(msm, 3),
             "quartics": nm, "matrix_bytes": ld * ld}
         del mbuf
+        # matrix multiplication mod 11 (Sec. 5 sizes): one warm-up and one timed product per size
+        for nmm in (5000, 10000, 20000):
+            g = torch.Generator(device=dev).manual_seed(nmm)
+            A = torch.randint(0, 11, (nmm, nmm), dtype=torch.uint8, device=dev, generator=g)
+            B = torch.randint(0, 11, (nmm, nmm), dtype=torch.uint8, device=dev, generator=g)
+            Cm = torch.empty(nmm, nmm, dtype=torch.uint8, device=dev)
+            qfs.matmul_mod(11, A, B, out=Cm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            qfs.matmul_mod(11, A, B, out=Cm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msm = max_over_ranks(e0.elapsed_time(e1))
+            extra[f"matmul-mod11-{nmm}"] = {"seconds": round(msm / 1e3, 5), "unit": "s per product",
+                                            "tops": round(2.0 * nmm ** 3 / (msm / 1e3) / 1e12, 2)}
+            del A, B, Cm
 
     # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step
     host_in = torch.from_numpy(f_np).pin_memory()

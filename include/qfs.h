@@ -188,6 +188,14 @@ int qfs_debug_stages(int p, const uint8_t *coeffs, int max_h, int form, int32_t 
    QFS_ERR_CUDA). */
 int qfs_theta_matrix(int p, int64_t n, const uint8_t *coeffs, uint8_t *M_out, cudaStream_t stream);
 
+/* Matrix multiplication mod p (the paper's Sec. 5 workload, square matrices mod 11): C = A B mod p.
+   A: device, n x k uint8, row-major; B: device, k x m uint8, row-major; C: device, n x m uint8, row-major; values
+   in [0, p), 2 <= p <= 256 (p need not be prime); all caller-owned.  Exact: products accumulate in int32 on the
+   int8 tensor cores and are reduced mod p.  Stream-ordered; may grow a library scratch buffer ((n + m) x k bytes
+   rounded up) with cudaMalloc.  Returns QFS_OK or QFS_ERR_INVALID_P, QFS_ERR_INVALID_N, QFS_ERR_NULL,
+   QFS_ERR_NO_MEMORY, QFS_ERR_CUDA (nothing enqueued on error).  n = 0 or m = 0 is a no-op; k = 0 zeroes C. */
+int qfs_matmul_mod(int p, int n, int m, int k, const uint8_t *A, const uint8_t *B, uint8_t *C, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ _SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
 _lib = None
 
 __all__ = ["build", "lib", "load", "Oracle", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
-           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "ROUTE_A", "ROUTE_R"]
+           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "matmul_mod", "ROUTE_A", "ROUTE_R"]
 
 ROUTE_A = 0
 ROUTE_R = 1
@@ -237,3 +237,10 @@ def theta_matrix(p, f):
         for c in np.nonzero((e >= 0).all(axis=1))[0]:
             M[r, c] = delta[index[tuple(e[c])]]
     return M
+
+
+def matmul_mod(p, A, B):
+    """C = A B mod p (Sec. 5): the integer matrix product (numpy, int64, exact for these sizes) reduced mod p."""
+    A = np.asarray(A, dtype=np.int64)
+    B = np.asarray(B, dtype=np.int64)
+    return (A @ B % p).astype(np.uint8)

@@ -10,6 +10,7 @@
 
 #include "../../include/qfs.h"
 #include "qfs_kernels.cuh"
+#include "qfs_matmul.cuh"
 #include "qfs_staged.cuh"
 #include "qfs_theta_matrix.cuh"
 
@@ -29,6 +30,8 @@ struct DeviceState {
   size_t staged_bytes = 0;
   int *which = nullptr;        // theta-matrix export: which workspace buffer holds each quartic's Delta
   int which_n = 0;
+  void *mm = nullptr;          // mod-p matrix multiplication: padded A and transposed B
+  size_t mm_bytes = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -365,6 +368,7 @@ int qfs_shutdown(void) {
     if (S.ctrl && cudaFree(S.ctrl) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.staged && cudaFree(S.staged) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.which && cudaFree(S.which) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.mm && cudaFree(S.mm) != cudaSuccess) rc = QFS_ERR_CUDA;
     S = DeviceState();
   }
   cudaSetDevice(cur);
@@ -594,4 +598,30 @@ extern "C" int qfs_theta_matrix(int p, int64_t n, const uint8_t *coeffs, uint8_t
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return QFS_OK;
+}
+
+extern "C" int qfs_matmul_mod(int p, int n, int m, int k, const uint8_t *A, const uint8_t *B, uint8_t *C,
+                              cudaStream_t stream) {
+  if (p < 2 || p > 256) return QFS_ERR_INVALID_P;
+  if (n < 0 || m < 0 || k < 0) return QFS_ERR_INVALID_N;
+  if (n == 0 || m == 0) return QFS_OK;
+  if (!C || (k > 0 && (!A || !B))) return QFS_ERR_NULL;
+  if (k == 0) return cudaMemsetAsync(C, 0, (size_t)n * m, stream) == cudaSuccess ? QFS_OK : QFS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  const size_t need = matmul_scratch_bytes(n, m, k);
+  if (S->mm_bytes < need) {
+    if (S->mm && cudaFree(S->mm) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    S->mm = nullptr;
+    S->mm_bytes = 0;
+    if (cudaMalloc(&S->mm, need) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return QFS_ERR_NO_MEMORY;
+    }
+    S->mm_bytes = need;
+  }
+  cudaError_t e = matmul_mod_launch(p, n, m, k, A, B, C, static_cast<uint8_t *>(S->mm), stream);
+  return e == cudaSuccess ? QFS_OK : cuda_fail(e);
 }

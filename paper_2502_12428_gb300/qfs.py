@@ -65,6 +65,7 @@ def _lib():
         L.qfs_debug_stages.argtypes = [c_int, vp, c_int, c_int, vp, vp, vp, vp, vp]
         L.qfs_heights_noalloc.argtypes = [c_int, i64, vp, c_int, vp, vp]
         L.qfs_theta_matrix.argtypes = [c_int, i64, vp, vp, vp]
+        L.qfs_matmul_mod.argtypes = [c_int, c_int, c_int, c_int, vp, vp, vp, vp]
         L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
         L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -73,7 +74,7 @@ def _lib():
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
-                     "qfs_theta_matrix"):
+                     "qfs_theta_matrix", "qfs_matmul_mod"):
             getattr(L, name).restype = c_int
         _LIB = L
         load_tile_table()
@@ -190,6 +191,23 @@ def theta_matrix(p, coeffs, out=None, stream=None):
     rc = _lib().qfs_theta_matrix(int(p), int(c2.shape[0]), c2.data_ptr(), out.data_ptr(), _stream(stream))
     _check(rc, "qfs_theta_matrix")
     return out[0] if single else out
+
+
+def matmul_mod(p, A, B, out=None, stream=None):
+    """qfs_matmul_mod: C = A B mod p for CUDA uint8 matrices A (n, k) and B (k, m) with values in [0, p)."""
+    _need_cuda(A, torch.uint8, "A")
+    _need_cuda(B, torch.uint8, "B")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError("A (n, k) and B (k, m) required")
+    A, B = A.contiguous(), B.contiguous()
+    n, k = A.shape
+    m = B.shape[1]
+    if out is None:
+        out = torch.empty(n, m, dtype=torch.uint8, device=A.device)
+    _need_cuda(out, torch.uint8, "out")
+    _check(_lib().qfs_matmul_mod(int(p), int(n), int(m), int(k), A.data_ptr(), B.data_ptr(), out.data_ptr(),
+                                 _stream(stream)), "qfs_matmul_mod")
+    return out
 
 
 TILE_TABLE = os.path.join(_HERE, "tile_table.json")

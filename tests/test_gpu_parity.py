@@ -398,3 +398,48 @@ def test_theta_matrix_applies_theta_and_rejects_bad_rows(qfs):
     assert not M[-1].any()
     with pytest.raises(qfs.QfsError):
         qfs.theta_matrix(4, dev_tensor(f))
+
+
+# ------------------------------------------------------------------------------------- matrix multiplication mod p
+@pytest.mark.parametrize("p,n,m,k", [(11, 1, 1, 1), (11, 17, 33, 65), (11, 300, 257, 129), (11, 128, 128, 64),
+                                     (11, 513, 130, 1000), (2, 200, 300, 77), (251, 140, 70, 300), (256, 64, 64, 64)])
+def test_matmul_mod_matches_oracle(qfs, p, n, m, k):
+    rng = np.random.default_rng(p * 1000 + n + m + k)
+    A = rng.integers(0, p, (n, k), dtype=np.uint8)
+    B = rng.integers(0, p, (k, m), dtype=np.uint8)
+    got = qfs.matmul_mod(p, dev_tensor(A), dev_tensor(B)).cpu().numpy()
+    assert np.array_equal(got, oracle.matmul_mod(p, A, B))
+
+
+def test_matmul_mod_long_k_reduces_between_tiles(qfs):
+    # k (p-1)^2 above 2^31 at p = 251: the accumulators are reduced between K tiles
+    p, n, m, k = 251, 16, 24, 40000
+    rng = np.random.default_rng(9)
+    A = rng.integers(p - 20, p, (n, k), dtype=np.uint8)
+    B = rng.integers(p - 20, p, (k, m), dtype=np.uint8)
+    got = qfs.matmul_mod(p, dev_tensor(A), dev_tensor(B)).cpu().numpy()
+    assert np.array_equal(got, oracle.matmul_mod(p, A, B))
+
+
+def test_matmul_mod_full_size_sampled(qfs):
+    # the paper's smallest size (5,000 x 5,000 mod 11); 256 entries checked one by one
+    p, n = 11, 5000
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.randint(0, p, (n, n), dtype=torch.uint8, device="cuda", generator=g)
+    B = torch.randint(0, p, (n, n), dtype=torch.uint8, device="cuda", generator=g)
+    C = qfs.matmul_mod(p, A, B).cpu().numpy()
+    An, Bn = A.cpu().numpy(), B.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for i, j in zip(rng.integers(0, n, 256), rng.integers(0, n, 256)):
+        assert C[i, j] == oracle.matmul_mod(p, An[i:i + 1], Bn[:, j:j + 1])[0, 0]
+
+
+def test_matmul_mod_edges(qfs):
+    z = torch.zeros(0, 5, dtype=torch.uint8, device="cuda")
+    assert qfs.matmul_mod(11, z, torch.zeros(5, 3, dtype=torch.uint8, device="cuda")).shape == (0, 3)
+    A = torch.ones(4, 0, dtype=torch.uint8, device="cuda")
+    C = qfs.matmul_mod(11, A, torch.ones(0, 6, dtype=torch.uint8, device="cuda"))
+    assert C.shape == (4, 6) and not C.any()
+    with pytest.raises(qfs.QfsError):
+        qfs.matmul_mod(1, torch.ones(2, 2, dtype=torch.uint8, device="cuda"), torch.ones(2, 2, dtype=torch.uint8,
+                                                                                         device="cuda"))

@@ -292,3 +292,22 @@ def test_theta_matrix_shape_and_sparsity():
     support = sum(int(((p * B[r][None, :] + (p - 1) - B) >= 0).all(axis=1).sum()) for r in range(len(B)))
     assert support == 16245
     assert np.count_nonzero(M) <= support
+
+
+# ------------------------------------------------------------------------------------- matrix multiplication mod p (Sec. 5)
+@pytest.mark.parametrize("p,n,m,k", [(11, 3, 4, 5), (2, 6, 1, 7), (251, 2, 3, 9)])
+def test_matmul_mod_brute_force(p, n, m, k):
+    rng = np.random.default_rng(p + n + m + k)
+    A = rng.integers(0, p, (n, k))
+    B = rng.integers(0, p, (k, m))
+    want = [[sum(int(A[i][t]) * int(B[t][j]) for t in range(k)) % p for j in range(m)] for i in range(n)]
+    assert np.array_equal(oracle.matmul_mod(p, A, B), np.array(want, np.uint8))
+
+
+def test_matmul_mod_identity_and_associativity():
+    p = 11
+    rng = np.random.default_rng(5)
+    A, B, C = (rng.integers(0, p, (8, 8)) for _ in range(3))
+    assert np.array_equal(oracle.matmul_mod(p, A, np.eye(8, dtype=np.int64)), A.astype(np.uint8))
+    assert np.array_equal(oracle.matmul_mod(p, oracle.matmul_mod(p, A, B), C),
+                          oracle.matmul_mod(p, A, oracle.matmul_mod(p, B, C)))
