@@ -357,6 +357,22 @@ def run_ours(args):
             extra[f"matmul-mod11-{nmm}"] = {"seconds": round(msm / 1e3, 5), "unit": "s per product",
                                             "tops": round(2.0 * nmm ** 3 / (msm / 1e3) / 1e12, 2)}
             del A, B, Cm
+        # exact powering over Z (Sec. 4 workload): degree-16 form, coefficients in {0..4}, powers 5, 10, 15
+        rng = np.random.default_rng(16)
+        f16 = rng.integers(0, 5, 969).astype(np.uint32)
+        for npow in (5, 10, 15):
+            n_out = (16 * npow + 3) * (16 * npow + 2) * (16 * npow + 1) // 6
+            limbs = torch.empty(n_out, 8, dtype=torch.int32, device=dev)
+            qfs.poly_power_limbs(16, f16, npow, out=limbs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            qfs.poly_power_limbs(16, f16, npow, out=limbs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra[f"poly-power-deg16-n{npow}"] = {"seconds": round(max_over_ranks(e0.elapsed_time(e1)) / 1e3, 5),
+                                                 "unit": "s per power", "output_terms": n_out}
+            del limbs
 
     # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step
     host_in = torch.from_numpy(f_np).pin_memory()

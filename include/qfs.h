@@ -196,6 +196,17 @@ int qfs_theta_matrix(int p, int64_t n, const uint8_t *coeffs, uint8_t *M_out, cu
    QFS_ERR_NO_MEMORY, QFS_ERR_CUDA (nothing enqueued on error).  n = 0 or m = 0 is a no-op; k = 0 zeroes C. */
 int qfs_matmul_mod(int p, int n, int m, int k, const uint8_t *A, const uint8_t *B, uint8_t *C, cudaStream_t stream);
 
+/* Exact n-th power over the integers of a homogeneous form of degree d in 4 variables (the paper's polynomial
+   powering workload of Sec. 4: a degree-16 form with coefficients in {0..4} raised to the powers 5 .. 15).
+   coeffs: HOST, C(d+3, 3) uint32 coefficients in descending lex order (read before the call returns).
+   out: device, C(d n + 3, 3) x 8 uint32: the coefficients of f^n in descending lex order, each a 256-bit unsigned
+   integer in 8 little-endian 32-bit limbs; caller-owned.  Requires d >= 1, n >= 1, d n <= 255 and
+   (sum of coefficients)^n < 2^215 (QFS_ERR_INVALID_N otherwise).  Exact: the power is taken modulo up to seven
+   word-size primes by number-theoretic transforms and recombined by the Chinese remainder theorem.
+   Stream-ordered; may grow a library scratch buffer (cudaMalloc).  Returns QFS_OK or QFS_ERR_INVALID_N,
+   QFS_ERR_NULL, QFS_ERR_NO_MEMORY, QFS_ERR_CUDA. */
+int qfs_poly_power(int d, const uint32_t *coeffs, int n, uint32_t *out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ _SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
 _lib = None
 
 __all__ = ["build", "lib", "load", "Oracle", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
-           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "matmul_mod", "ROUTE_A", "ROUTE_R"]
+           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "matmul_mod", "poly_power",
+           "form_monomials", "ROUTE_A", "ROUTE_R"]
 
 ROUTE_A = 0
 ROUTE_R = 1
@@ -244,3 +245,24 @@ def matmul_mod(p, A, B):
     A = np.asarray(A, dtype=np.int64)
     B = np.asarray(B, dtype=np.int64)
     return (A @ B % p).astype(np.uint8)
+
+
+def form_monomials(deg):
+    """Exponent tuples (x1, x2, x3, x4) of the degree-deg monomials in descending lex order."""
+    return [(a, b, c, deg - a - b - c) for a in range(deg, -1, -1) for b in range(deg - a, -1, -1)
+            for c in range(deg - a - b, -1, -1)]
+
+
+def poly_power(d, coeffs, n):
+    """f^n over the integers (Sec. 4's powering workload) by repeated multiplication with Python integers: the
+    plain definition, for small cases.  coeffs in descending lex order; returns the coefficients of f^n likewise."""
+    f = {e: int(c) for e, c in zip(form_monomials(d), coeffs) if int(c)}
+    acc = {(0, 0, 0, 0): 1}
+    for _ in range(n):
+        nxt = {}
+        for ea, ca in acc.items():
+            for eb, cb in f.items():
+                k = (ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2], ea[3] + eb[3])
+                nxt[k] = nxt.get(k, 0) + ca * cb
+        acc = nxt
+    return [acc.get(e, 0) for e in form_monomials(d * n)]

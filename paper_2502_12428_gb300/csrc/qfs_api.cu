@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -11,6 +12,7 @@
 #include "../../include/qfs.h"
 #include "qfs_kernels.cuh"
 #include "qfs_matmul.cuh"
+#include "qfs_polypow.cuh"
 #include "qfs_staged.cuh"
 #include "qfs_theta_matrix.cuh"
 
@@ -32,6 +34,8 @@ struct DeviceState {
   int which_n = 0;
   void *mm = nullptr;          // mod-p matrix multiplication: padded A and transposed B
   size_t mm_bytes = 0;
+  void *pp = nullptr;          // polynomial powering: transform, twiddles, residues, input
+  size_t pp_bytes = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -369,6 +373,7 @@ int qfs_shutdown(void) {
     if (S.staged && cudaFree(S.staged) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.which && cudaFree(S.which) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.mm && cudaFree(S.mm) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.pp && cudaFree(S.pp) != cudaSuccess) rc = QFS_ERR_CUDA;
     S = DeviceState();
   }
   cudaSetDevice(cur);
@@ -623,5 +628,39 @@ extern "C" int qfs_matmul_mod(int p, int n, int m, int k, const uint8_t *A, cons
     S->mm_bytes = need;
   }
   cudaError_t e = matmul_mod_launch(p, n, m, k, A, B, C, static_cast<uint8_t *>(S->mm), stream);
+  return e == cudaSuccess ? QFS_OK : cuda_fail(e);
+}
+
+extern "C" int qfs_poly_power(int d, const uint32_t *coeffs, int n, uint32_t *out, cudaStream_t stream) {
+  if (d < 1 || n < 1 || d * n > 255) return QFS_ERR_INVALID_N;
+  if (!coeffs || !out) return QFS_ERR_NULL;
+  const int n_in = tet(d + 1);
+  double sum = 0;
+  for (int i = 0; i < n_in; ++i) sum += coeffs[i];
+  // every output coefficient is at most (sum of the coefficients)^n
+  const double log2_bound = sum <= 1.0 ? 1.0 : n * std::log2(sum);
+  if (log2_bound >= 32.0 * kPolyPowLimbs - 1) return QFS_ERR_INVALID_N;
+  const int nprimes = polypow_primes(log2_bound);
+  if (nprimes == 0) return QFS_ERR_INVALID_N;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState *S = nullptr;
+  int rc = device_state(&S);
+  if (rc) return rc;
+  const size_t need = polypow_scratch_words(d, n, nprimes) * sizeof(uint32_t);
+  if (S->pp_bytes < need) {
+    if (S->pp && cudaFree(S->pp) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    S->pp = nullptr;
+    S->pp_bytes = 0;
+    if (cudaMalloc(&S->pp, need) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return QFS_ERR_NO_MEMORY;
+    }
+    S->pp_bytes = need;
+  }
+  uint32_t *scratch = static_cast<uint32_t *>(S->pp);
+  uint32_t *cdev = scratch + (need / sizeof(uint32_t) - n_in - 16);   // the input sits at the end of the scratch
+  cudaError_t e = cudaMemcpyAsync(cdev, coeffs, sizeof(uint32_t) * n_in, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = polypow_launch(d, n, nprimes, cdev, out, scratch, stream);
   return e == cudaSuccess ? QFS_OK : cuda_fail(e);
 }

@@ -6,6 +6,7 @@ no CPU fallback: if the library is not built, or no CUDA device is present, ever
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +67,7 @@ def _lib():
         L.qfs_heights_noalloc.argtypes = [c_int, i64, vp, c_int, vp, vp]
         L.qfs_theta_matrix.argtypes = [c_int, i64, vp, vp, vp]
         L.qfs_matmul_mod.argtypes = [c_int, c_int, c_int, c_int, vp, vp, vp, vp]
+        L.qfs_poly_power.argtypes = [c_int, vp, c_int, vp, vp]
         L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
         L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -74,7 +76,7 @@ def _lib():
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
-                     "qfs_theta_matrix", "qfs_matmul_mod"):
+                     "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power"):
             getattr(L, name).restype = c_int
         _LIB = L
         load_tile_table()
@@ -208,6 +210,28 @@ def matmul_mod(p, A, B, out=None, stream=None):
     _check(_lib().qfs_matmul_mod(int(p), int(n), int(m), int(k), A.data_ptr(), B.data_ptr(), out.data_ptr(),
                                  _stream(stream)), "qfs_matmul_mod")
     return out
+
+
+def poly_power_limbs(d, coeffs, n, out=None, stream=None, device=None):
+    """qfs_poly_power: the n-th power over Z of the degree-d form with nonnegative integer coefficients `coeffs`
+    (host sequence, descending lex).  Returns a CUDA int64 tensor (C(d n + 3, 3), 8) of 32-bit limbs (little endian)
+    holding each 256-bit coefficient; poly_power() turns them into Python integers."""
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint32).reshape(-1))
+    n_out = (d * n + 3) * (d * n + 2) * (d * n + 1) // 6
+    if out is None:
+        out = torch.empty(n_out, 8, dtype=torch.int32, device=device or "cuda")
+    _need_cuda(out, torch.int32, "out")
+    _check(_lib().qfs_poly_power(int(d), c.ctypes.data, int(n), out.data_ptr(), _stream(stream)), "qfs_poly_power")
+    return out
+
+
+def poly_power(d, coeffs, n, stream=None):
+    """The coefficients of f^n as Python integers (descending lex order)."""
+    limbs = poly_power_limbs(d, coeffs, n, stream=stream).cpu().numpy().astype(np.uint32).astype(object)
+    out = limbs[:, 0].copy()
+    for l in range(1, 8):
+        out = out + (limbs[:, l] << (32 * l))
+    return list(out)
 
 
 TILE_TABLE = os.path.join(_HERE, "tile_table.json")

@@ -443,3 +443,53 @@ def test_matmul_mod_edges(qfs):
     with pytest.raises(qfs.QfsError):
         qfs.matmul_mod(1, torch.ones(2, 2, dtype=torch.uint8, device="cuda"), torch.ones(2, 2, dtype=torch.uint8,
                                                                                          device="cuda"))
+
+
+# ------------------------------------------------------------------------------------- exact powering over Z
+def _multinomial(es):
+    from math import factorial
+    out = factorial(sum(es))
+    for e in es:
+        out //= factorial(e)
+    return out
+
+
+def _eval_mod(cs, deg, pt, mod):
+    pw = [[pow(x, k, mod) for k in range(deg + 1)] for x in pt]
+    acc = 0
+    for c, e in zip(cs, oracle.form_monomials(deg)):
+        acc = (acc + c * pw[0][e[0]] * pw[1][e[1]] * pw[2][e[2]] * pw[3][e[3]]) % mod
+    return acc
+
+
+@pytest.mark.parametrize("d,n", [(1, 100), (16, 6)])
+def test_poly_power_multinomial_closed_form(qfs, d, n):
+    # (x1+x2+x3+x4)^d to the n-th power: every coefficient is a multinomial coefficient (up to 200 bits)
+    f = [_multinomial(e) for e in oracle.form_monomials(d)]
+    got = qfs.poly_power(d, f, n)
+    assert got == [_multinomial(e) for e in oracle.form_monomials(d * n)]
+
+
+@pytest.mark.parametrize("d,n", [(4, 3), (16, 2), (16, 1)])
+def test_poly_power_matches_definition(qfs, d, n):
+    rng = np.random.default_rng(d * 100 + n)
+    f = [int(x) for x in rng.integers(0, 5, len(oracle.form_monomials(d)))]
+    assert qfs.poly_power(d, f, n) == oracle.poly_power(d, f, n)
+
+
+@pytest.mark.parametrize("n", [5, 15])
+def test_poly_power_paper_workload_evaluation(qfs, n):
+    # degree 16, coefficients in {0..4}: f^n(pt) = f(pt)^n at an integer point, modulo 2^127 - 1
+    rng = np.random.default_rng(16 + n)
+    f = [int(x) for x in rng.integers(0, 5, len(oracle.form_monomials(16)))]
+    P = qfs.poly_power(16, f, n)
+    mod = (1 << 127) - 1
+    pt = (3, 5, 7, 11)
+    assert _eval_mod(P, 16 * n, pt, mod) == pow(_eval_mod(f, 16, pt, mod), n, mod)
+
+
+def test_poly_power_errors(qfs):
+    with pytest.raises(qfs.QfsError):
+        qfs.poly_power(16, [1] * 969, 16)   # degree 256
+    with pytest.raises(qfs.QfsError):
+        qfs.poly_power(1, [2 ** 31] * 4, 8)   # coefficients too large for 256 bits

@@ -311,3 +311,32 @@ def test_matmul_mod_identity_and_associativity():
     assert np.array_equal(oracle.matmul_mod(p, A, np.eye(8, dtype=np.int64)), A.astype(np.uint8))
     assert np.array_equal(oracle.matmul_mod(p, oracle.matmul_mod(p, A, B), C),
                           oracle.matmul_mod(p, A, oracle.matmul_mod(p, B, C)))
+
+
+# ------------------------------------------------------------------------------------- powering over Z (Sec. 4)
+def _multinomial(es):
+    from math import factorial
+    out = factorial(sum(es))
+    for e in es:
+        out //= factorial(e)
+    return out
+
+
+def test_poly_power_sum_of_variables_is_multinomial():
+    """(x1+x2+x3+x4)^2 to the 3rd power is (x1+...+x4)^6: every coefficient is a multinomial coefficient."""
+    d, n = 2, 3
+    f = [_multinomial(e) for e in oracle.form_monomials(d)]
+    got = oracle.poly_power(d, f, n)
+    assert got == [_multinomial(e) for e in oracle.form_monomials(d * n)]
+
+
+def test_poly_power_evaluation_identity():
+    """f^n evaluated at integer points equals f(point)^n."""
+    rng = np.random.default_rng(4)
+    d, n = 4, 3
+    f = [int(x) for x in rng.integers(0, 5, len(oracle.form_monomials(d)))]
+    P = oracle.poly_power(d, f, n)
+    for pt in [(1, 2, 3, 4), (2, -1, 5, 0), (7, 1, 1, -3)]:
+        ev = lambda cs, deg: sum(c * pt[0] ** e[0] * pt[1] ** e[1] * pt[2] ** e[2] * pt[3] ** e[3]
+                                 for c, e in zip(cs, oracle.form_monomials(deg)))
+        assert ev(P, d * n) == ev(f, d) ** n
