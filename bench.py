@@ -115,14 +115,17 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------- helpers
+# the sources the fused dp4a kernel is compiled from (its launch shape comes from qfs_api.cu's occupancy query)
+FUSED_KERNEL_SOURCES = ("qfs_layout.cuh", "qfs_common.cuh", "qfs_sweep.cuh", "qfs_engine.cuh", "qfs_kernels.cuh",
+                        "qfs_form_dp4a.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_12428_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        path = os.path.join(csrc, f)
-        if os.path.isfile(path):
-            with open(path, "rb") as fh:
-                h.update(fh.read())
+    for f in FUSED_KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
