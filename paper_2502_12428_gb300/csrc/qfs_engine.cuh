@@ -317,7 +317,8 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
       const int total = pre[kMaxUpar];
       const int *stab = sm.slot_tab[tab];
       if (FORM == 2) {
-        // tiles: (slice du, column group of 16, word pair wp); word pairs of a group cover its longest column
+        // tiles: (slice du, column group of 16, word pair wp); word pairs of a group cover the data of its longest
+        // column (s/8 + 1 pairs); the padding words after them are cleared below
         int tpre[2 * kMaxUpar + 1];
         tpre[0] = 0;
 #pragma unroll
@@ -325,7 +326,7 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
           const int du = i >> 1, grp = i & 1;
           const int hi = min(s_last, u + du);
           const int sg = s0 + 16 * grp;
-          tpre[i + 1] = tpre[i] + ((du < nU && sg <= hi) ? 2 * chunks_of(min(hi, sg + 15)) : 0);
+          tpre[i + 1] = tpre[i] + ((du < nU && sg <= hi) ? half_chunks_of(min(hi, sg + 15)) : 0);
         }
         const int ntiles = tpre[2 * kMaxUpar];
         const int group = lane >> 2, tig = lane & 3;
@@ -384,6 +385,15 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
               if (DEBUG && LAST) dbg.G[o] = ghalf | (gother << 16);
             }
           }
+        }
+        // padding words of each column past the word pairs its group's tiles cover (columns hold s + 4 entries)
+        for (int i = threadIdx.x; i < nU * 32; i += nthreads) {
+          const int du = i >> 5, s = s0 + (i & 31), uo = u + du;
+          const int hi = min(s_last, uo);
+          if (s > hi) continue;
+          const int sg = s0 + 16 * ((s - s0) >> 4);
+          for (int w = 2 * half_chunks_of(min(hi, sg + 15)); w < 4 * chunks_of(s); ++w)
+            out[sm.SW[uo] + colw(s) + w] = 0u;
         }
       } else
       for (int it = warp; it * 32 < total; it += nwarps) {
