@@ -488,11 +488,11 @@ inline size_t theta_guarded_words(int p) {
   return (size_t)host_sw(D + 1) + (size_t)theta_gsw_extra(D + 1);
 }
 
-// Workspace buffer stride (see qfs_common.cuh): a padded degree-D form, or for p >= 11 theta's guarded copy of
-// Delta, which is larger (p <= 7 streams Delta through shared memory instead).
+// Workspace buffer stride (see qfs_common.cuh): a padded degree-D form, or theta's guarded copy of Delta, which is
+// larger (p = 7 streams Delta through shared memory instead and needs no copy).
 inline size_t workspace_stride_words(int p) {
   const size_t padded = (size_t)padded_words(4 * p * (p - 1));
-  return (p <= 7 ? padded : std::max(padded, theta_guarded_words(p))) + kGuardWords;
+  return (p == 7 ? padded : std::max(padded, theta_guarded_words(p))) + kGuardWords;
 }
 
 // Reversed g columns: column (u_c, s_c) holds g[u_c, s_c, s_c - j] at byte j (j <= s_c), zero-padded to whole words.
@@ -505,10 +505,11 @@ __host__ __device__ constexpr int theta_r_words() {
   for (int u = 0; u <= 4 * (P - 1); ++u) r += rcolw(u + 1);
   return r;
 }
-// Theta for p <= 7 streams Delta slice by slice through shared memory (two guarded slice slots); larger primes
-// gather from the guarded copy in global memory (a slice of Delta does not fit twice in shared memory).
+// Theta at p = 7 streams Delta slice by slice through shared memory (two guarded slice slots): the guarded copies
+// of all CTAs (1.7 MB each) would not stay in L2.  At p <= 5 they do (0.3 MB each), and the per-output gather from
+// the guarded copy in global memory is faster; at p >= 11 a slice of Delta does not fit twice in shared memory.
 template <int P>
-__host__ __device__ constexpr bool theta_streams() { return P <= 7; }
+__host__ __device__ constexpr bool theta_streams() { return P == 7; }
 // a slice slot: columns 0 .. D with the guards of the guarded layout
 template <int P>
 __host__ __device__ constexpr int theta_slot_words() { return kThetaGuardWords * (4 * P * (P - 1) + 2) + colw(4 * P * (P - 1) + 1); }
@@ -660,7 +661,7 @@ __device__ __forceinline__ void theta_unit(const uint32_t *__restrict__ slot, co
   }
 }
 
-// One theta step with Delta (padded, degree D, global memory) streamed through shared memory, p <= 7.  Round e_u
+// One theta step with Delta (padded, degree D, global memory) streamed through shared memory (p = 7).  Round e_u
 // copies slice e_u into a guarded slot (16-byte cp.async, double buffered) and serves every output slice u_r whose
 // g slice u_c = p u_r + 3(p-1) - e_u exists, as warp-wide units (u_r, g column s_c) whose lanes take consecutive
 // outputs and run the same number of words; partial sums go to shared int32 accumulators.  Every Delta byte is read from global memory
@@ -1164,7 +1165,7 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   }
   if (DEBUG)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
-  // A6 + A7.  p <= 7: Delta streams through shared memory; larger p: a guarded copy of Delta, built in the buffer
+  // A6 + A7.  p = 7: Delta streams through shared memory; other p: a guarded copy of Delta, built in the buffer
   // that does not hold Delta, is gathered from directly
   uint32_t *dg = delta == bufA ? bufB : bufA;
   if (!theta_streams<P>()) {
