@@ -7,8 +7,9 @@
 // input slices v upwards.  Input slice v feeds output slices u = v .. v+4 (tap pairs uI = u - v): the lane loads
 // the five input columns s - sI (sI = 0..4) of slice v once (eight bytes plus the word before them), builds the
 // byte windows once, and adds every tap pair (uI, sI) with uI >= sI into the accumulator set of output u = v + uI.
-// Five accumulator sets, set k holding output slice v + k; after slice v, set 0 (output v) is complete and is
-// reduced, packed and stored, and the sets move down one place.
+// Five accumulator sets, set k holding output slice v + k; after slice v, set 0 (output v) is complete, moves to a
+// sixth set and is reduced, packed and stored during the next slice (while that slice's loads are in flight), and
+// the sets move down one place.
 //
 // Compared with staging the slices through shared memory, every input word is loaded once per lane and slice
 // rather than once per tap pair, windows are built once per input column rather than once per pair, and the
@@ -81,7 +82,7 @@ __device__ __forceinline__ void load_slice(const uint32_t *__restrict__ in, cons
 template <int J, int SI, int FORM, bool DENSE>
 __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32_t (&tw)[15], uint32_t a44,
                                             const int (&taps)[35], uint32_t mask, uint32_t colmask,
-                                            int (&acc)[5][8]) {
+                                            int (&acc)[6][8]) {
   if (!DENSE && !((colmask >> SI) & 1u)) return;  // every tap pair of this input column is zero
   if (FORM == 1) {
     // window of output t = 8h + 4q + r: bytes in(t-3 .. t) = bytes r+1 .. r+4 of (word q-1 of the half-chunk,
@@ -140,7 +141,7 @@ __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32
 // epilogue), store, and clear the set.
 template <int P, int J, bool LAST, bool DEBUG>
 __device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem &sm, const Lane &L, int u,
-                                         const uint8_t *gs, int (&acc)[5][8], bool &bad, DebugPtrs dbg) {
+                                         const uint8_t *gs, int (&acc)[6][8], bool &bad, DebugPtrs dbg) {
   using Pr = Prime<P>;
   if (L.valid && u >= L.s) {
     uint32_t w[2] = {0u, 0u}, gw[2] = {0u, 0u};
@@ -174,22 +175,6 @@ __device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem 
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) acc[J][j] = 0;
-}
-
-// One slice step with v = J (mod 5): load slice v, add it to the output sets, finalize output v.
-template <int P, int J, int FORM, bool DENSE, bool LAST, bool DEBUG>
-__device__ __forceinline__ void step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, const Smem &sm,
-                                     const Lane &L, int v, const uint8_t *gs, const uint32_t (&tw)[15], uint32_t a44,
-                                     const int (&taps)[35], uint32_t mask, uint32_t colmask, int (&acc)[5][8],
-                                     bool &bad, DebugPtrs dbg) {
-  uint32_t X[5][3];
-  load_slice<P>(in, sm, L, v, X);
-  column_macs<J, 0, FORM, DENSE>(X[0], tw, a44, taps, mask, colmask, acc);
-  column_macs<J, 1, FORM, DENSE>(X[1], tw, a44, taps, mask, colmask, acc);
-  column_macs<J, 2, FORM, DENSE>(X[2], tw, a44, taps, mask, colmask, acc);
-  column_macs<J, 3, FORM, DENSE>(X[3], tw, a44, taps, mask, colmask, acc);
-  column_macs<J, 4, FORM, DENSE>(X[4], tw, a44, taps, mask, colmask, acc);
-  finalize<P, J, LAST, DEBUG>(out, sm, L, v, gs, acc, bad, dbg);
 }
 
 // Next task of the current product for this warp (warp-uniform), or -1 when the queue is empty.  Tasks are handed
@@ -251,16 +236,26 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
     L.out_off = colw(L.s) + 2 * L.h;
     // the last item of column s also clears the padding half-chunks after it (2 chunks_of(s) - (s/8 + 1) of them)
     L.pad = L.h == half_chunks_of(L.s) - 1 ? 2 * chunks_of(L.s) - half_chunks_of(L.s) : 0;
-    int acc[5][8];
+    int acc[6][8];
 #pragma unroll
-    for (int a = 0; a < 5; ++a)
+    for (int a = 0; a < 6; ++a)
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[a][j] = 0;
     const int v0 = max(0, s_first - 4);
     // slices v0 .. m_in; after each slice the accumulator sets move down one place (set 0 always holds the output
     // slice that the current input slice completes), so one copy of the step serves every slice
+    // output slice v-1 waits in set 5 and is finalized while slice v's loads are in flight
     for (int v = v0; v <= m_in; ++v) {
-      step<P, 0, FORM, DENSE, LAST, DEBUG>(in, out, sm, L, v, gs, tw, a44, taps, mask, colmask, acc, bad, dbg);
+      uint32_t X[5][3];
+      load_slice<P>(in, sm, L, v, X);
+      if (v > v0) finalize<P, 5, LAST, DEBUG>(out, sm, L, v - 1, gs, acc, bad, dbg);
+      column_macs<0, 0, FORM, DENSE>(X[0], tw, a44, taps, mask, colmask, acc);
+      column_macs<0, 1, FORM, DENSE>(X[1], tw, a44, taps, mask, colmask, acc);
+      column_macs<0, 2, FORM, DENSE>(X[2], tw, a44, taps, mask, colmask, acc);
+      column_macs<0, 3, FORM, DENSE>(X[3], tw, a44, taps, mask, colmask, acc);
+      column_macs<0, 4, FORM, DENSE>(X[4], tw, a44, taps, mask, colmask, acc);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[5][j] = acc[0][j];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -268,7 +263,8 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[4][j] = 0;
     }
-    // output slices m_in+1 .. m_out take no further input: they sit in sets 0 .. 3
+    // output slice m_in (set 5), then m_in+1 .. m_out, which take no further input (sets 0 .. 3)
+    finalize<P, 5, LAST, DEBUG>(out, sm, L, m_in, gs, acc, bad, dbg);
     finalize<P, 0, LAST, DEBUG>(out, sm, L, m_in + 1, gs, acc, bad, dbg);
     finalize<P, 1, LAST, DEBUG>(out, sm, L, m_in + 2, gs, acc, bad, dbg);
     finalize<P, 2, LAST, DEBUG>(out, sm, L, m_in + 3, gs, acc, bad, dbg);
