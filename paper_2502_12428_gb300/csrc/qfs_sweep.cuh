@@ -7,9 +7,9 @@
 // input slices v upwards.  Input slice v feeds output slices u = v .. v+4 (tap pairs uI = u - v): the lane loads
 // the five input columns s - sI (sI = 0..4) of slice v once (eight bytes plus the word before them), builds the
 // byte windows once, and adds every tap pair (uI, sI) with uI >= sI into the accumulator set of output u = v + uI.
-// Five accumulator sets, set k holding output slice v + k; after slice v, set 0 (output v) is complete, moves to a
-// sixth set and is reduced, packed and stored during the next slice (while that slice's loads are in flight), and
-// the sets move down one place.
+// Six accumulator sets: five hold the output slices v .. v + 4 that slice v feeds, the sixth the output slice
+// completed by the previous slice, which is reduced, packed and stored while this slice's loads are in flight.
+// The dense dp4a path takes the slices two at a time, so the sets move down two places per pair.
 //
 // Compared with staging the slices through shared memory, every input word is loaded once per lane and slice
 // rather than once per tap pair, windows are built once per input column rather than once per pair, and the
@@ -66,7 +66,7 @@ struct Lane {
 template <int P>
 __device__ __forceinline__ void load_slice(const uint32_t *__restrict__ in, const Smem &sm, const Lane &L, int v,
                                            uint32_t (&X)[5][3]) {
-  const int base = sm.SW[v];
+  const int base = sm.SW[max(v, 0)];  // v = -1 (a leading slice with no columns) reads only guard words
 #pragma unroll
   for (int sI = 0; sI < 5; ++sI) {
     const bool ex = ((L.colok >> sI) & 1u) && (L.s - sI <= v);
@@ -78,7 +78,7 @@ __device__ __forceinline__ void load_slice(const uint32_t *__restrict__ in, cons
   }
 }
 
-// Contributions of input column s - SI of slice v (words X) to the output sets J + uI (mod 5), uI = SI .. 4.
+// Contributions of input column s - SI of slice v (words X) to the output sets J + uI, uI = SI .. 4.
 template <int J, int SI, int FORM, bool DENSE>
 __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32_t (&tw)[15], uint32_t a44,
                                             const int (&taps)[35], uint32_t mask, uint32_t colmask,
@@ -99,7 +99,7 @@ __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32
     for (int uI = SI; uI < 5; ++uI) {
       const int pi = uI * (uI + 1) / 2 + SI;
       if (DENSE || ((mask >> pi) & 1u)) {
-        const int set = (J + uI) % 5;
+        const int set = J + uI;
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -109,7 +109,7 @@ __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32
     }
     if (SI == 4 && (DENSE || ((mask >> 14) & 1u))) {
       // tap (4, 4, 4) reads in(t - 4) = byte r of word q-1
-      const int set = (J + 4) % 5;
+      const int set = J + 4;
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -125,7 +125,7 @@ __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32
     for (int uI = SI; uI < 5; ++uI) {
       const int pi = uI * (uI + 1) / 2 + SI;
       if (DENSE || ((mask >> pi) & 1u)) {
-        const int set = (J + uI) % 5;
+        const int set = J + uI;
 #pragma unroll
         for (int tI = 0; tI <= SI; ++tI) {
           const int a = taps[tet(uI) + tri(SI) + tI];
@@ -134,6 +134,99 @@ __device__ __forceinline__ void column_macs(const uint32_t (&X)[3], const uint32
         }
       }
     }
+  }
+}
+
+// Byte windows of one input column: W[q][r] holds in(t - 3 .. t) (byte k = in(t - 3 + k)) for the output
+// t = 8h + 4q + r, from the words X = {word 2h - 1, 2h, 2h + 1} of the column.
+__device__ __forceinline__ void column_windows(const uint32_t (&X)[3], uint32_t (&W)[2][4]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    W[q][0] = __byte_perm(X[q], X[q + 1], 0x4321u);
+    W[q][1] = __byte_perm(X[q], X[q + 1], 0x5432u);
+    W[q][2] = __byte_perm(X[q], X[q + 1], 0x6543u);
+    W[q][3] = X[q + 1];
+  }
+}
+
+// dp4a form, every tap pair present: slice v into the sets J .. J + 4.  A pair (uI, sI) has sI + 1 taps, so the
+// windows of the pairs (1, 1) and (uI, 2) leave their byte 0 unused; it carries the single tap of (uI, 0) instead
+// (byte 0 of the window <- in_0(t), byte 0 of the tap word <- a(uI, 0, 0), merged into tw by the caller).  That is
+// 12 dp4a per output in place of 16, for 16 byte permutes per slice.
+template <int J>
+__device__ __forceinline__ void slice_macs_merged(const uint32_t (&X)[5][3], const uint32_t (&tw)[15], uint32_t a44,
+                                                  int (&acc)[6][8]) {
+  uint32_t W0[2][4];
+  column_windows(X[0], W0);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      acc[J][4 * q + r] = (int)__dp4a(W0[q][r], tw[0], (unsigned)acc[J][4 * q + r]);
+  {
+    uint32_t W1[2][4];
+    column_windows(X[1], W1);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t m = __byte_perm(W1[q][r], W0[q][r], 0x3217u);
+        acc[J + 1][4 * q + r] = (int)__dp4a(m, tw[2], (unsigned)acc[J + 1][4 * q + r]);
+      }
+#pragma unroll
+    for (int uI = 2; uI < 5; ++uI)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          acc[J + uI][4 * q + r] = (int)__dp4a(W1[q][r], tw[tri(uI) + 1], (unsigned)acc[J + uI][4 * q + r]);
+  }
+  {
+    uint32_t W2[2][4];
+    column_windows(X[2], W2);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t m = __byte_perm(W2[q][r], W0[q][r], 0x3217u);
+#pragma unroll
+        for (int uI = 2; uI < 5; ++uI)
+          acc[J + uI][4 * q + r] = (int)__dp4a(m, tw[tri(uI) + 2], (unsigned)acc[J + uI][4 * q + r]);
+      }
+  }
+#pragma unroll
+  for (int sI = 3; sI < 5; ++sI) {
+    uint32_t W[2][4];
+    column_windows(X[sI], W);
+#pragma unroll
+    for (int uI = sI; uI < 5; ++uI)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          acc[J + uI][4 * q + r] = (int)__dp4a(W[q][r], tw[tri(uI) + sI], (unsigned)acc[J + uI][4 * q + r]);
+  }
+  // tap (4, 4, 4) reads in_4(t - 4) = byte r of word q - 1
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      acc[J + 4][4 * q + r] = (int)__dp4a(X[4][q], a44 << (8 * r), (unsigned)acc[J + 4][4 * q + r]);
+}
+
+// Slice v into the sets J .. J + 4.
+template <int J, int FORM, bool DENSE>
+__device__ __forceinline__ void slice_macs(const uint32_t (&X)[5][3], const uint32_t (&tw)[15], uint32_t a44,
+                                           const int (&taps)[35], uint32_t mask, uint32_t colmask,
+                                           int (&acc)[6][8]) {
+  if (FORM == 1 && DENSE) {
+    slice_macs_merged<J>(X, tw, a44, acc);
+  } else {
+    column_macs<J, 0, FORM, DENSE>(X[0], tw, a44, taps, mask, colmask, acc);
+    column_macs<J, 1, FORM, DENSE>(X[1], tw, a44, taps, mask, colmask, acc);
+    column_macs<J, 2, FORM, DENSE>(X[2], tw, a44, taps, mask, colmask, acc);
+    column_macs<J, 3, FORM, DENSE>(X[3], tw, a44, taps, mask, colmask, acc);
+    column_macs<J, 4, FORM, DENSE>(X[4], tw, a44, taps, mask, colmask, acc);
   }
 }
 
@@ -147,7 +240,7 @@ __device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem 
     uint32_t w[2] = {0u, 0u}, gw[2] = {0u, 0u};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      int G = acc[J][j] % Pr::p2;  // acc >= 0; outputs past the column's end are zero
+      int G = (int)((uint32_t)acc[J][j] % (uint32_t)Pr::p2);  // acc >= 0; outputs past the column's end are zero
       if (LAST) {
         const int t = 8 * L.h + j;
         if (DEBUG) gw[j >> 2] |= (uint32_t)G << (8 * (j & 3));
@@ -215,6 +308,12 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
 #pragma unroll
     for (int k = 0; k < 15; ++k) tw[k] = sm.tapword[k];
     a44 = (uint32_t)sm.taps[34];
+    if (DENSE) {
+      // byte 0 of the pairs (1, 1) and (uI, 2) carries a(uI, 0, 0) (byte 3 of the pair (uI, 0)); see slice_macs_merged
+      tw[2] |= tw[1] >> 24;
+#pragma unroll
+      for (int uI = 2; uI < 5; ++uI) tw[tri(uI) + 2] |= tw[tri(uI)] >> 24;
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 35; ++k) taps[k] = sm.taps[k];
@@ -242,26 +341,52 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[a][j] = 0;
     const int v0 = max(0, s_first - 4);
-    // slices v0 .. m_in; after each slice the accumulator sets move down one place (set 0 always holds the output
-    // slice that the current input slice completes), so one copy of the step serves every slice
-    // output slice v-1 waits in set 5 and is finalized while slice v's loads are in flight
-    for (int v = v0; v <= m_in; ++v) {
-      uint32_t X[5][3];
-      load_slice<P>(in, sm, L, v, X);
-      if (v > v0) finalize<P, 5, LAST, DEBUG>(out, sm, L, v - 1, gs, acc, bad, dbg);
-      column_macs<0, 0, FORM, DENSE>(X[0], tw, a44, taps, mask, colmask, acc);
-      column_macs<0, 1, FORM, DENSE>(X[1], tw, a44, taps, mask, colmask, acc);
-      column_macs<0, 2, FORM, DENSE>(X[2], tw, a44, taps, mask, colmask, acc);
-      column_macs<0, 3, FORM, DENSE>(X[3], tw, a44, taps, mask, colmask, acc);
-      column_macs<0, 4, FORM, DENSE>(X[4], tw, a44, taps, mask, colmask, acc);
+    if constexpr (FORM == 1 && DENSE) {
+      // Slices are taken two at a time; an odd count starts one slice early, at a slice none of whose columns
+      // exist for this warp (every lane has s >= s_first, so s - sI > v0 - 1), which reads only the zero guard
+      // words.  Before the pair (v, v + 1), set k holds output slice v + k (k = 0 .. 4, set 4 zero) and set 5
+      // holds output v - 1, complete: it is finalized while slice v's loads are in flight, and output v (set 0)
+      // while slice v + 1's are.  Slice v adds into sets 0 .. 4 and slice v + 1 into sets 1 .. 5; the sets then
+      // move down two places (set k <- set k + 2 mod 6), so one copy of the pair serves every slice.
+      const int vb = v0 - ((m_in - v0 + 1) & 1);
+      for (int v = vb; v <= m_in; v += 2) {
+        uint32_t X[5][3];
+        load_slice<P>(in, sm, L, v, X);
+        if (v > vb) finalize<P, 5, LAST, DEBUG>(out, sm, L, v - 1, gs, acc, bad, dbg);
+        slice_macs<0, FORM, DENSE>(X, tw, a44, taps, mask, colmask, acc);
+        load_slice<P>(in, sm, L, v + 1, X);
+        finalize<P, 0, LAST, DEBUG>(out, sm, L, v, gs, acc, bad, dbg);
+        slice_macs<1, FORM, DENSE>(X, tw, a44, taps, mask, colmask, acc);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[5][j] = acc[0][j];
+        for (int j = 0; j < 8; ++j) {
+          // set 0 is zero (finalized): 0 <- 2 <- 4 <- 0 and 1 <- 3 <- 5 <- 1
+          const int t1 = acc[1][j];
+          acc[0][j] = acc[2][j];
+          acc[2][j] = acc[4][j];
+          acc[4][j] = 0;
+          acc[1][j] = acc[3][j];
+          acc[3][j] = acc[5][j];
+          acc[5][j] = t1;
+        }
+      }
+    } else {
+      // One slice at a time (the int32 form and the sparse path hold more live registers): after slice v the
+      // sets move down one place, and output v waits in set 5 to be finalized while slice v + 1's loads are in
+      // flight.
+      for (int v = v0; v <= m_in; ++v) {
+        uint32_t X[5][3];
+        load_slice<P>(in, sm, L, v, X);
+        if (v > v0) finalize<P, 5, LAST, DEBUG>(out, sm, L, v - 1, gs, acc, bad, dbg);
+        slice_macs<0, FORM, DENSE>(X, tw, a44, taps, mask, colmask, acc);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int j = 0; j < 8; ++j) acc[5][j] = acc[0][j];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[a][j] = acc[a + 1][j];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[4][j] = 0;
+          for (int j = 0; j < 8; ++j) acc[a][j] = acc[a + 1][j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[4][j] = 0;
+      }
     }
     // output slice m_in (set 5), then m_in+1 .. m_out, which take no further input (sets 0 .. 3)
     finalize<P, 5, LAST, DEBUG>(out, sm, L, m_in, gs, acc, bad, dbg);
