@@ -14,6 +14,7 @@
 #include "qfs_matmul.cuh"
 #include "qfs_polypow.cuh"
 #include "qfs_staged.cuh"
+#include "qfs_screen.cuh"
 #include "qfs_theta_matrix.cuh"
 
 namespace qfs {
@@ -27,7 +28,7 @@ struct DeviceState {
   size_t total_mem = 0;
   void *ws = nullptr;          // persistent-CTA workspaces
   size_t ws_bytes = 0;
-  void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32), [16]: stats (2 x u64)
+  void *ctrl = nullptr;        // [0]: work counter (u64), [8]: status (u32), [16]: stats (2 x u64), [32]: survivors (u64)
   void *staged = nullptr;      // staged-engine survivor buffers
   size_t staged_bytes = 0;
   int *which = nullptr;        // theta-matrix export: which workspace buffer holds each quartic's Delta
@@ -36,6 +37,8 @@ struct DeviceState {
   size_t mm_bytes = 0;
   void *pp = nullptr;          // polynomial powering: transform, twiddles, residues, input
   size_t pp_bytes = 0;
+  void *list = nullptr;        // survivors of the height-1 screen (int64 launch items)
+  size_t list_bytes = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -96,6 +99,23 @@ int ensure_workspace(DeviceState &S, size_t bytes) {
     return QFS_ERR_NO_MEMORY;
   }
   S.ws_bytes = bytes;
+  return QFS_OK;
+}
+
+int ensure_list(DeviceState &S, size_t bytes) {
+  if (S.list_bytes >= bytes) return QFS_OK;
+  if (S.list) {
+    cudaError_t e = cudaFree(S.list);
+    S.list = nullptr;
+    S.list_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (cudaMalloc(&S.list, bytes) != cudaSuccess) {
+    S.list = nullptr;
+    (void)cudaGetLastError();
+    return QFS_ERR_NO_MEMORY;
+  }
+  S.list_bytes = bytes;
   return QFS_OK;
 }
 
@@ -323,7 +343,18 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   prm.stats = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(S->ctrl) + 16);
   prm.ws = reinterpret_cast<uint32_t *>(S->ws);
   prm.ws_words = plan.ws_words;
-  cudaError_t e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
+  // height-1 screen first: the persistent launch then runs only the quartics that pass it
+  rc = ensure_list(*S, (size_t)n_items * sizeof(int64_t));
+  if (rc) return rc;
+  auto *n_list = reinterpret_cast<unsigned long long *>(static_cast<char *>(S->ctrl) + 32);
+  cudaError_t e = cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int64_t screen_ctas = std::min<int64_t>((n_items + 7) / 8, (int64_t)S->sms * 8);
+  e = screen_launch(prm, max_p, static_cast<int64_t *>(S->list), n_list, (int)screen_ctas, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  prm.list = static_cast<const int64_t *>(S->list);
+  prm.n_list = n_list;
+  e = cudaMemsetAsync(prm.counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   e = form_fused(form, prm, plan.grid, plan.smem, stream, form == QFS_FORM_INT8TC && max_p <= 5);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -355,6 +386,10 @@ int qfs_plan_prepare(int p, int64_t n_hint) {
     rc = make_plan(*S, form, p, n, nullptr, plan, smem_bytes_for(p, tile_for(p), uses_ring_chain(form, p)));
     if (rc) return rc;
   }
+  if (n_hint > 0) {
+    rc = ensure_list(*S, (size_t)n_hint * sizeof(int64_t));
+    if (rc) return rc;
+  }
   cudaError_t e = cudaDeviceSynchronize();
   return e == cudaSuccess ? QFS_OK : cuda_fail(e);
 }
@@ -374,6 +409,7 @@ int qfs_shutdown(void) {
     if (S.which && cudaFree(S.which) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.mm && cudaFree(S.mm) != cudaSuccess) rc = QFS_ERR_CUDA;
     if (S.pp && cudaFree(S.pp) != cudaSuccess) rc = QFS_ERR_CUDA;
+    if (S.list && cudaFree(S.list) != cudaSuccess) rc = QFS_ERR_CUDA;
     S = DeviceState();
   }
   cudaSetDevice(cur);

@@ -1211,6 +1211,8 @@ struct FusedParams {
   uint32_t *ws;                       // workspace: a guard, then 2 buffers of ws_words (the stride) per CTA
   size_t ws_words;
   int power_mode;                     // 0: chain (Algorithm 1 literally), 1: identity shortcut, 2: reduced theta
+  const int64_t *list;                // if set: the items to run (the survivors of the height-1 screen) ...
+  const unsigned long long *n_list;   // ... and their count; if null, every item 0 .. n_items-1 runs
 };
 
 // SMALL: an int8 tensor form launch whose primes are all <= 5; the kernel then needs no code for larger primes and
@@ -1230,12 +1232,16 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
   uint32_t *bufA, *bufB;
   cta_buffers(prm.ws, prm.ws_words, bufA, bufB);
   DebugPtrs dbg{nullptr, nullptr, nullptr, nullptr};
+  const int64_t n_run = prm.list ? (int64_t)*prm.n_list : prm.n_items;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) sm.item = (int64_t)atomicAdd(prm.counter, 1ull);
+    if (threadIdx.x == 0) {
+      const int64_t k = (int64_t)atomicAdd(prm.counter, 1ull);
+      sm.item = k < n_run ? (prm.list ? prm.list[k] : k) : -1;
+    }
     __syncthreads();
     const int64_t item = sm.item;
-    if (item >= prm.n_items) break;
+    if (item < 0) break;
     int gi = 0;
     while (gi + 1 < prm.n_groups && item >= prm.g[gi + 1].item_begin) ++gi;
     const FusedGroup &G = prm.g[gi];
