@@ -645,7 +645,31 @@ __device__ __forceinline__ void theta_unit(const uint32_t *__restrict__ slot, co
   uint32_t rv[NW];
 #pragma unroll
   for (int k = 0; k < NW; ++k) rv[k] = Rc[k];
-  for (int r = r0 + lane; r < r1; r += 32) {
+  // two outputs per lane at a time (r and r + 32), so that their shared-memory round trips overlap
+  int r = r0 + lane;
+  for (; r + 32 < r1; r += 64) {
+    int byte[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const uint32_t x = rst[r + 32 * i];
+      const int sr = (int)((x >> 8) & 255u), tr = (int)(x >> 16);
+      byte[i] = gofs[P * sr + 2 * (P - 1) - sc] + P * tr + (P - 1) - sc;
+    }
+    uint32_t dv[2][NW + 1];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int k = 0; k <= NW; ++k) dv[i][k] = slot[(byte[i] >> 2) + k];
+    unsigned a[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        a[i] = __dp4a(__funnelshift_r(dv[i][k], dv[i][k + 1], 8u * (unsigned)(byte[i] & 3)), rv[k], a[i]);
+    atomicAdd(acc + r, (int)a[0]);
+    atomicAdd(acc + r + 32, (int)a[1]);
+  }
+  if (r < r1) {
     const uint32_t x = rst[r];
     const int sr = (int)((x >> 8) & 255u), tr = (int)(x >> 16);
     const int byte = gofs[P * sr + 2 * (P - 1) - sc] + P * tr + (P - 1) - sc;
