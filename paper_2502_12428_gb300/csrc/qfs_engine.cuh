@@ -635,64 +635,48 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
   return __syncthreads_or(any ? 1 : 0) != 0;
 }
 
-// One (u_r, s_c) unit of a streamed theta round: lanes take the outputs r0 + lane, r0 + lane + 32, ... < r1 of slice
-// u_r; each sums NW words of its Delta window (guarded slot) against the NW words of g's reversed column s_c.
-// gofs[e_s] = byte offset of Delta column e_s in a slot; rst[r] = u_r | s_r << 8 | t_r << 16.
+// Up to four g columns s_c = sc0 .. sc1 of a streamed theta round, all of NW words (sc0 / 4 == sc1 / 4), for the
+// output r = (u_r, s_r, t_r) of this lane: each column s_c inside the lane's range [lo, hi] adds the lane's Delta
+// window (NW + 1 words of the guarded slot, shifted to the window's first byte) against the NW words of g's
+// reversed column s_c, which are the same for every lane.  ebase = p s_r + 2(p-1), so the Delta column is
+// e_s = ebase - s_c; tbase = p t_r + (p-1), the window's last byte in that column.  All loads of the four columns
+// are issued before the first product.
 template <int P, int NW>
-__device__ __forceinline__ void theta_unit(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rc,
-                                           const int *__restrict__ gofs, const uint32_t *__restrict__ rst,
-                                           int *acc, int r0, int r1, int sc, int lane) {
-  uint32_t rv[NW];
+__device__ __forceinline__ unsigned theta_seg(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rb,
+                                              const int *__restrict__ gofs, int sc0, int sc1, int lo, int hi,
+                                              int ebase, int tbase, unsigned a) {
+  uint32_t dv[4][NW + 1], rv[4][NW];
+  unsigned sh[4];
 #pragma unroll
-  for (int k = 0; k < NW; ++k) rv[k] = Rc[k];
-  // two outputs per lane at a time (r and r + 32), so that their shared-memory round trips overlap
-  int r = r0 + lane;
-  for (; r + 32 < r1; r += 64) {
-    int byte[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const uint32_t x = rst[r + 32 * i];
-      const int sr = (int)((x >> 8) & 255u), tr = (int)(x >> 16);
-      byte[i] = gofs[P * sr + 2 * (P - 1) - sc] + P * tr + (P - 1) - sc;
-    }
-    uint32_t dv[2][NW + 1];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int k = 0; k <= NW; ++k) dv[i][k] = slot[(byte[i] >> 2) + k];
-    unsigned a[2] = {0u, 0u};
-#pragma unroll
-    for (int k = 0; k < NW; ++k)
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-        a[i] = __dp4a(__funnelshift_r(dv[i][k], dv[i][k + 1], 8u * (unsigned)(byte[i] & 3)), rv[k], a[i]);
-    atomicAdd(acc + r, (int)a[0]);
-    atomicAdd(acc + r + 32, (int)a[1]);
-  }
-  if (r < r1) {
-    const uint32_t x = rst[r];
-    const int sr = (int)((x >> 8) & 255u), tr = (int)(x >> 16);
-    const int byte = gofs[P * sr + 2 * (P - 1) - sc] + P * tr + (P - 1) - sc;
+  for (int j = 0; j < 4; ++j) {
+    const int sc = sc0 + j;
+    const bool in = sc <= sc1;
+    const bool on = in && sc >= lo && sc <= hi;
+    const int byte = on ? gofs[ebase - sc] + tbase - sc : 0;
+    sh[j] = 8u * (unsigned)(byte & 3);
     const uint32_t *dw = slot + (byte >> 2);
-    const unsigned sh = 8u * (unsigned)(byte & 3);
-    uint32_t dv[NW + 1];
 #pragma unroll
-    for (int k = 0; k <= NW; ++k) dv[k] = dw[k];
-    unsigned a = 0;
+    for (int k = 0; k <= NW; ++k) dv[j][k] = on ? dw[k] : 0u;
+    const uint32_t *rw = Rb + rcolw(sc);
 #pragma unroll
-    for (int k = 0; k < NW; ++k) a = __dp4a(__funnelshift_r(dv[k], dv[k + 1], sh), rv[k], a);
-    atomicAdd(acc + r, (int)a);
+    for (int k = 0; k < NW; ++k) rv[j][k] = in ? rw[k] : 0u;
   }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < NW; ++k) a = __dp4a(__funnelshift_r(dv[j][k], dv[j][k + 1], sh[j]), rv[j][k], a);
+  return a;
 }
 
 // One theta step with Delta (padded, degree D, global memory) streamed through shared memory (p = 7).  Round e_u
 // copies slice e_u into a guarded slot (16-byte cp.async, double buffered) and serves every output slice u_r whose
-// g slice u_c = p u_r + 3(p-1) - e_u exists, as warp-wide units (u_r, g column s_c) whose lanes take consecutive
-// outputs and run the same number of words; partial sums go to shared int32 accumulators.  Every Delta byte is read from global memory
-// once per step.  Returns whether some output is nonzero (same value in every thread).
+// g slice u_c = p u_r + 3(p-1) - e_u exists, in blocks of 32 consecutive outputs (one per lane) that sum over the
+// g columns in registers; each round's sums go to shared int32 accumulators.  Every Delta byte is read from global
+// memory once per step.  Returns whether some output is nonzero (same value in every thread).
 template <int P>
 __device__ __noinline__ bool theta_stream(const uint32_t *__restrict__ delta, const Smem &sm,
                                           const uint8_t *__restrict__ g, uint8_t *__restrict__ gn, uint32_t *ring) {
+  static_assert(P <= 7, "g columns of at most 7 words");
   using Pr = Prime<P>;
   constexpr int d = Pr::d, D = Pr::D, ld = Pr::ld;
   constexpr int SLOT = theta_slot_words<P>();
@@ -762,29 +746,48 @@ __device__ __noinline__ bool theta_stream(const uint32_t *__restrict__ delta, co
     const int ur_lo = max(0, (base + P - 1) / P);
     const int ur_hi = min(d, base + d >= 0 ? (base + d) / P : -1);
     if (ur_lo > ur_hi) continue;
-    // work units (u_r, s_c), one warp each: the outputs of slice u_r whose Delta column e_s = p s_r + 2(p-1) - s_c
-    // lies in slice e_u, a contiguous run of packed outputs; every lane of the unit runs the same word count
-    int nunits = 0;
-    for (int ur = ur_lo; ur <= ur_hi; ++ur) nunits += P * ur - base + 1;   // s_c = 0 .. u_c
-    for (int unit = warp; unit < nunits; unit += nwarps) {
-      int ur = ur_lo, sc = unit;
-      while (sc > P * ur - base) { sc -= P * ur - base + 1; ++ur; }
-      const int uc = P * ur - base;
-      const int sr_lo = max(0, sc - 2 * (P - 1) > 0 ? (sc - 2 * (P - 1) + P - 1) / P : 0);
-      const int nhi = eu + sc - 2 * (P - 1);   // e_s <= e_u  <=>  p s_r <= nhi
-      const int sr_hi = min(ur, nhi >= 0 ? nhi / P : -1);
-      if (sr_lo > sr_hi) continue;
-      const uint32_t *Rc = R + RSW[uc] + rcolw(sc);
-      const int r0 = tet(ur) + tri(sr_lo), r1 = tet(ur) + tri(sr_hi + 1);
-      switch (sc >> 2) {   // words of g's reversed column s_c: s_c / 4 + 1 <= p
-        case 0: theta_unit<P, 1>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        case 1: theta_unit<P, 2>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        case 2: theta_unit<P, 3>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        case 3: theta_unit<P, 4>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        case 4: theta_unit<P, 5>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        case 5: theta_unit<P, 6>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
-        default: theta_unit<P, 7>(slot, Rc, gofs, rst, acc, r0, r1, sc, lane); break;
+    // blocks of 32 consecutive outputs of a slice u_r, one warp each (lane = output): a lane sums, over every g
+    // column s_c whose Delta column e_s = p s_r + 2(p-1) - s_c lies in slice e_u, in registers, and adds the total
+    // to its output once per round; the warp runs the union of its lanes' column ranges, four columns at a time
+    int nblocks = 0;
+    for (int ur = ur_lo; ur <= ur_hi; ++ur) nblocks += (tri(ur + 1) + 31) >> 5;
+    for (int blk = warp; blk < nblocks; blk += nwarps) {
+      int ur = ur_lo, b = blk;
+      for (;;) {
+        const int nb = (tri(ur + 1) + 31) >> 5;
+        if (b < nb) break;
+        b -= nb;
+        ++ur;
       }
+      const int uc = P * ur - base;   // in [0, d] for ur in [ur_lo, ur_hi]
+      const int i = 32 * b + lane;
+      const bool act = i < tri(ur + 1);
+      const int r = tet(ur) + i;
+      int lo = 1 << 30, hi = -1, ebase = 0, tbase = 0;
+      if (act) {
+        const uint32_t x = rst[r];
+        ebase = P * (int)((x >> 8) & 255u) + 2 * (P - 1);
+        tbase = P * (int)(x >> 16) + (P - 1);
+        lo = max(0, ebase - eu);   // e_s <= e_u
+        hi = min(uc, ebase);       // e_s >= 0
+      }
+      const int wlo = __reduce_min_sync(0xffffffffu, lo), whi = __reduce_max_sync(0xffffffffu, hi);
+      if (wlo > whi) continue;
+      const uint32_t *Rb = R + RSW[uc];
+      unsigned a = 0;
+      for (int q = wlo >> 2; q <= (whi >> 2); ++q) {
+        const int sc0 = max(wlo, 4 * q), sc1 = min(whi, 4 * q + 3);
+        switch (q) {   // words of g's reversed column: s_c / 4 + 1 <= p
+          case 0: a = theta_seg<P, 1>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 1: a = theta_seg<P, 2>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 2: a = theta_seg<P, 3>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 3: a = theta_seg<P, 4>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 4: a = theta_seg<P, 5>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 5: a = theta_seg<P, 6>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          default: a = theta_seg<P, 7>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+        }
+      }
+      if (act && a != 0u) atomicAdd(acc + r, (int)a);
     }
   }
   cp_async_wait_all();
@@ -1192,14 +1195,15 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   // A6 + A7.  p = 7: Delta streams through shared memory; other p: a guarded copy of Delta, built in the buffer
   // that does not hold Delta, is gathered from directly
   uint32_t *dg = delta == bufA ? bufB : bufA;
-  if (!theta_streams<P>()) {
+  if constexpr (!theta_streams<P>()) {
     delta_to_guarded<P>(delta, dg, sm);
     __syncthreads();
   }
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
-    const bool nonzero = theta_streams<P>() ? theta_stream<P>(delta, sm, g, g2, ring)
-                                            : theta_gather<P>(dg, sm, g, g2, ring);
+    bool nonzero;
+    if constexpr (theta_streams<P>()) nonzero = theta_stream<P>(delta, sm, g, g2, ring);
+    else nonzero = theta_gather<P>(dg, sm, g, g2, ring);
     theta_steps = h - 1;
     if (DEBUG)
       for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = g2[i];

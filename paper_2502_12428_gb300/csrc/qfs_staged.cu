@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 2) stage_theta(StagedChunk c, const 
   for (unsigned slot = blockIdx.x; slot < total; slot += gridDim.x) {
     if (!c.active[slot]) continue;
     for (int i = threadIdx.x; i < Pr::ld; i += blockDim.x) gs[i] = gin[(size_t)slot * Pr::ld + i];
-    if (theta_streams<P>()) {
+    if constexpr (theta_streams<P>()) {
       __syncthreads();
       theta_stream<P>(c.G + slot * gwords, *sm, gs, gn, ring);
     } else {
