@@ -420,7 +420,7 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": {"value": round(world * n / (e2e_ms / 1e3), 1), "unit": "quartics/s",
                     "h2d_bytes_per_step": int(n * 35), "d2h_bytes_per_step": int(n)},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,   # per step: the height-1 screen and the persistent fused kernel
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
