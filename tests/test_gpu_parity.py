@@ -227,6 +227,41 @@ def test_device_status_clean(qfs):
     assert qfs.read_status() == 0
 
 
+# ------------------------------------------------------------------------------------- height-1 screen
+def test_screen_settles_whole_batches(qfs):
+    # a batch that the screen settles entirely leaves the persistent launch with no survivors
+    p = 5
+    f, h = find_rows(p, 600, 6100, lambda x: x == 1, 300)
+    qfs.read_stats()
+    assert np.array_equal(gpu_heights(qfs, p, f), h)
+    assert qfs.read_stats()[0] == 0
+    bad = f.copy()
+    bad[:, 7] = p
+    assert (gpu_heights(qfs, p, bad) == -1).all()
+    assert qfs.read_stats()[0] == 0
+    # and a batch with no height-1 row at all: every row reaches the persistent launch
+    g, hg = find_rows(p, 2000, 6150, lambda x: x != 1, 120)
+    assert np.array_equal(gpu_heights(qfs, p, g), hg)
+    assert qfs.read_stats()[0] == len(g)
+
+
+def test_screen_survivor_count_matches_oracle(qfs):
+    p = 7
+    f = inputs.dense(p, 1500, 6200)
+    want = oracle.heights(p, f)
+    qfs.read_stats()
+    assert np.array_equal(gpu_heights(qfs, p, f), want)
+    assert qfs.read_stats()[0] == int((want != 1).sum())
+
+
+@pytest.mark.parametrize("p", [3, 11, 13])
+def test_screen_fedder_decision(qfs, p):
+    # with max_h = 1 only the height-1 test decides a row: F = f^((p-1)/2) takes 0, 4 and 5 products in the warp
+    f = np.concatenate([inputs.dense(p, 1200, 6300 + p), inputs.sparse(p, 400, 6400 + p)])
+    want = oracle.heights(p, f, max_h=1)
+    assert np.array_equal(gpu_heights(qfs, p, f, max_h=1), want)
+
+
 # ------------------------------------------------------------------------------------- staged engine
 @pytest.mark.parametrize("p,n", [(3, 500), (5, 3000), (7, 600)])
 def test_staged_engine_matches_fused_and_oracle(qfs, p, n):
