@@ -97,7 +97,9 @@ typedef struct {
 } qfs_options_t;
 
 /* Heights of n quartics over F_p.  coeffs: device, n x 35 uint8.  heights_out: device, n int8.
-   Returns QFS_OK or an error status (nothing enqueued on error). */
+   Returns QFS_OK or an error status (nothing enqueued on error).
+   The fused engine enqueues two kernels: a height-1 screen (Fedder's criterion, one warp per quartic), which writes
+   1 or -1 for the rows it settles and lists the others, then the persistent launch over the listed rows. */
 int qfs_heights(int p, int64_t n, const uint8_t *coeffs, int max_h, int8_t *heights_out, cudaStream_t stream);
 
 /* Several batches, possibly over different primes, in one persistent launch (groups is a host array of
@@ -113,8 +115,9 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
 int qfs_set_default_form(int form);
 
 /* Prepares the current device for prime p: checks the device, tunes launch shapes and allocates the workspace
-   a fused launch over up to n_hint quartics needs (n_hint <= 0: a full-device launch).  Synchronous; it may call
-   cudaMalloc.  Optional: the first qfs_heights call does the same lazily. */
+   a fused launch over up to n_hint quartics needs (n_hint <= 0: a full-device launch; the survivor list of the
+   height-1 screen is sized only when n_hint > 0).  Synchronous; it may call cudaMalloc.  Optional: the first
+   qfs_heights call does the same lazily. */
 int qfs_plan_prepare(int p, int64_t n_hint);
 
 /* Chain tile shape per prime (process-wide; the autotuner below picks it on the device at hand).
@@ -160,7 +163,9 @@ int qfs_last_cuda_error(void);
    each call clears the part that must start at zero.  Calls whose kernels overlap on the GPU (for example calls
    on two different streams of one device) share the array and race: keep them ordered on one stream.
    Returns QFS_ERR_NO_MEMORY when one persistent CTA's workspace does not fit in 64 MiB (p = 13); otherwise it
-   runs as many CTAs as fit (p = 7: 39, p = 11: 2), so large p runs slower here than through qfs_heights. */
+   runs as many CTAs as fit (p = 7: 39, p = 11: 2), so large p runs slower here than through qfs_heights.  It has
+   no height-1 screen (the survivor list would need n x 8 bytes): every quartic enters the persistent launch,
+   which takes the same decisions. */
 int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int max_h, int8_t *heights_out,
                         cudaStream_t stream);
 
