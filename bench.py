@@ -245,7 +245,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TOP/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"qfs::fused_kernel<{ {'int32': 0, 'dp4a': 1, 'int8tc': 2}[args.form]}>",
-                "ops_per_launch": 2 * macs, "peak_basis": f"{SMS} SMs x {LANES[args.form]} int MAC lanes x "
+                "ops_per_launch": 2 * macs,
+                "duration_basis": "CUDA events around the call on its stream: the height-1 screen (about 0.5 % "
+                                  "of the launch list) and the persistent kernel",
+                "peak_basis": f"{SMS} SMs x {LANES[args.form]} int MAC lanes x "
                 f"{SM_MAX_MHZ:.0f} MHz x 2 ops (nominal; 1 MAC = 2 ops)"}
 
     forms_out = {args.form: {"value": round(value, 1), "ms_per_step": round(ms_step, 3),
