@@ -155,6 +155,25 @@ def test_full_size_sparse_p5(qfs):
     sampled_check(qfs, p, f, h, n_uniform=3000, seed=3)
 
 
+@pytest.mark.slow
+def test_full_size_mixed_sampled(qfs):
+    # the mixed-prime workload at full size in one launch (131,072 quartics at p = 5 and at p = 7, 4,096 at p = 11,
+    # each followed by its PGL_4 image): every group sampled against the oracle, every image with its row's height
+    seed = inputs.config_seed(5)
+    groups, rows = [], []
+    for p, n, kind in inputs.CONFIG_SIZES[5]:
+        f = inputs.dense(p, n, seed + p)
+        A = inputs.pgl4_matrices(p, n, seed + 100 + p)
+        both = np.concatenate([f, inputs.substitute(f, A, p)])
+        groups.append((p, dev_tensor(both), None))
+        rows.append((p, n, both))
+    outs = [o.cpu().numpy() for o in qfs.heights_multi(groups)]
+    for (p, n, both), out in zip(rows, outs):
+        assert out.min() >= 0 and out.max() <= 10
+        assert np.array_equal(out[:n], out[n:])
+        sampled_check(qfs, p, both, out, n_uniform=1500 if p < 11 else 200, seed=p)
+
+
 # ------------------------------------------------------------------------------------- mixed primes in one launch
 def test_multi_group_mixed_and_pgl4(qfs):
     groups, wants, pairs = [], [], []
