@@ -15,7 +15,6 @@ reduction ("scaling": "weak").  --impl reference times the CPU oracle (the liter
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
