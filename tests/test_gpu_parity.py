@@ -194,6 +194,17 @@ def test_multi_group_mixed_and_pgl4(qfs):
         assert np.array_equal(qfs.heights(p, t).cpu().numpy(), out)
 
 
+def test_multi_group_with_empty_groups(qfs):
+    # empty groups take no part in the launch; a call whose groups are all empty enqueues nothing
+    f = inputs.dense(7, 300, 7900)
+    empty = torch.zeros(0, 35, dtype=torch.uint8, device="cuda:0")
+    outs = qfs.heights_multi([(5, empty, None), (7, dev_tensor(f), None), (11, empty, None)])
+    assert outs[0].numel() == 0 and outs[2].numel() == 0
+    assert np.array_equal(outs[1].cpu().numpy(), oracle.heights(7, f))
+    outs = qfs.heights_multi([(5, empty, None), (7, empty, None)])
+    assert all(o.numel() == 0 for o in outs)
+
+
 # ------------------------------------------------------------------------------------- edge cases and errors
 def test_edge_cases(qfs):
     p = 5
