@@ -138,13 +138,26 @@ int qfs_shutdown(void);
 
 /* Copies the device status word of the current device's last launches into *status_out (0 = no check failed;
    bit 0 = an exact division by p in Delta_1 found a remainder; bit 1 = the theta test saw an out-of-range value),
-   then clears it.  Synchronises the current device. */
+   then clears it.  The word covers every launch since the last call, qfs_heights_noalloc's included (that entry
+   point keeps its own word in its fixed array; this call ORs it in and clears it too).  Synchronises the current
+   device. */
 int qfs_read_status(uint32_t *status_out);
 
 /* Work counters of the current device's launches since the last call: quartics that passed the height-1 test
    (so ran the full power chain, Delta_1 and at least one theta step unless max_h = 1) and theta steps run in
-   total.  Clears them.  Synchronises the current device.  Used to turn timings into algorithmic work rates. */
+   total, qfs_heights_noalloc's launches included.  Clears them.  Synchronises the current device.  Used to turn
+   timings into algorithmic work rates. */
 int qfs_read_stats(uint64_t *survivors, uint64_t *theta_steps);
+
+/* Measured multiply-add rates of the current device's integer paths, the denominators of the height kernels'
+   rooflines (the paper has no counterpart; this is a measurement aid).  macs_per_s: host, 3 doubles, filled with
+   the multiply-accumulates per second of independent IMAD chains ([0]: the int32 form's instruction), IDP4A chains
+   ([1]: 4 MACs each, the dp4a form's) and mma.sync m16n8k32 s8 tiles ([2]: the int8 tensor form's), each the best
+   of three timed launches of 8 CTAs per SM.  sms / max_clock_khz (host, may be NULL): the device's SM count and
+   its maximum SM clock, so that rates turn into per-SM-per-clock figures.  Allocates and frees a small device
+   buffer; synchronous; takes about a tenth of a second.  Returns QFS_OK, QFS_ERR_NULL, QFS_ERR_NO_MEMORY or
+   QFS_ERR_CUDA. */
+int qfs_int_peaks(double *macs_per_s, int *sms, int *max_clock_khz);
 
 /* Human-readable text for a status code (static storage). */
 const char *qfs_strerror(int status);
@@ -160,8 +173,10 @@ int qfs_last_cuda_error(void);
    array of device memory that the library declares statically: every GPU that loads libqfs holds it until the
    process exits.  The first call on a device looks up that array's device address (cudaGetSymbolAddress), so
    make the first call on each device before any stream capture.  The array keeps the previous call's contents;
-   each call clears the part that must start at zero.  Calls whose kernels overlap on the GPU (for example calls
-   on two different streams of one device) share the array and race: keep them ordered on one stream.
+   each call clears the part that must start at zero (its work-queue counter).  The device check word and the
+   work counters of these calls accumulate in the array until qfs_read_status and qfs_read_stats read and clear
+   them, together with those of the other entry points.  Calls whose kernels overlap on the GPU (for example
+   calls on two different streams of one device) share the array and race: keep them ordered on one stream.
    Returns QFS_ERR_NO_MEMORY when one persistent CTA's workspace does not fit in 64 MiB (p = 13); otherwise it
    runs as many CTAs as fit (p = 7: 39, p = 11: 2), so large p runs slower here than through qfs_heights.  It has
    no height-1 screen (the survivor list would need n x 8 bytes): every quartic enters the persistent launch,

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqfs.so")
 SOURCES = ["qfs_api.cu", "qfs_form_int32.cu", "qfs_form_dp4a.cu", "qfs_form_int8tc.cu", "qfs_debug_int32.cu",
            "qfs_debug_dp4a.cu", "qfs_debug_int8tc.cu", "qfs_noalloc.cu", "qfs_staged.cu", "qfs_theta_matrix.cu",
-           "qfs_matmul.cu", "qfs_polypow.cu", "qfs_screen.cu"]
+           "qfs_matmul.cu", "qfs_polypow.cu", "qfs_screen.cu", "qfs_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

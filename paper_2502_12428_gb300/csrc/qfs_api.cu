@@ -19,6 +19,8 @@
 
 namespace qfs {
 
+int noalloc_take_counters(uint32_t *status, unsigned long long *stats);   // qfs_noalloc.cu
+
 namespace {
 
 struct DeviceState {
@@ -508,8 +510,11 @@ int qfs_read_stats(uint64_t *survivors, uint64_t *theta_steps) {
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaMemset(reinterpret_cast<char *>(S->ctrl) + 16, 0, 16);
   if (e != cudaSuccess) return cuda_fail(e);
-  *survivors = v[0];
-  *theta_steps = v[1];
+  unsigned long long na[2] = {0, 0};
+  rc = noalloc_take_counters(nullptr, na);
+  if (rc) return rc;
+  *survivors = v[0] + na[0];
+  *theta_steps = v[1] + na[1];
   return QFS_OK;
 }
 
@@ -526,7 +531,10 @@ int qfs_read_status(uint32_t *status_out) {
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaMemset(reinterpret_cast<char *>(S->ctrl) + 8, 0, 4);
   if (e != cudaSuccess) return cuda_fail(e);
-  *status_out = v;
+  uint32_t na = 0;
+  rc = noalloc_take_counters(&na, nullptr);
+  if (rc) return rc;
+  *status_out = v | na;
   return QFS_OK;
 }
 

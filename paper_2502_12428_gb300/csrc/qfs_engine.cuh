@@ -1116,11 +1116,10 @@ __device__ __noinline__ int reduced_height(Smem &sm, uint8_t *gs, uint8_t *gn, u
       decode_packed(r, ur, sr, tr);
       const int eu0 = P * ur + 3 * (P - 1), es0 = P * sr + 2 * (P - 1), et0 = P * tr + (P - 1);
       unsigned a = 0;
-      for (int col = lane; col < tri(d + 1); col += 32) {
-        int uc = (int)((sqrtf(8.0f * (float)col + 1.0f) - 1.0f) * 0.5f);
-        while (tri(uc) > col) --uc;
-        while (tri(uc + 1) <= col) ++uc;
-        const int sc = col - tri(uc);
+      // g column col = tri(uc) + sc of this lane, advanced 32 columns at a time
+      int uc = (isqrt(8 * lane + 1) - 1) >> 1, sc = lane - tri(uc);
+      for (int col = lane; col < tri(d + 1); col += 32, sc += 32) {
+        while (sc > uc) sc -= ++uc;
         const int eu = eu0 - uc, es = es0 - sc;
         if (eu < 0 || eu > d1 || es < 0 || es > eu) continue;
         const int tlo = max(0, et0 - es), thi = min(sc, et0);

@@ -50,6 +50,32 @@ struct Prime {
   static constexpr int witness = tet(wu) + tri(ws) + wt;
 };
 
+// floor(sqrt(x)) for 0 <= x < 2^30, digit by digit (integer arithmetic only).
+__host__ __device__ inline int isqrt(int x) {
+  int r = 0, bit = 1 << 28;
+  while (bit > x) bit >>= 2;
+  while (bit != 0) {
+    if (x >= r + bit) {
+      x -= r + bit;
+      r = (r >> 1) + bit;
+    } else {
+      r >>= 1;
+    }
+    bit >>= 2;
+  }
+  return r;
+}
+
+// floor(cbrt(x)) for 0 <= x < 2^30, by bisection.
+__host__ __device__ inline int icbrt(int x) {
+  int lo = 0, hi = 1024;   // lo^3 <= x < hi^3
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)mid * mid * mid <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // SW table on the host (sizes, admission) -- same recurrence as the device copy.
 inline int64_t host_sw(int u) {
   int64_t acc = 0;
@@ -72,15 +98,14 @@ __device__ __forceinline__ void build_sw(int *SW, int n) {
 
 // Flat chunk index h of one slice (h = F(s) + c) -> column s and chunk c.  F(s) = E(s+4) - 4, so h + 4 is the
 // flat index of chunk c of "column" s + 4 under E, which inverts in closed form.
-__device__ __forceinline__ void decode_chunk(int h, int &s, int &c) {
+__host__ __device__ inline void decode_chunk(int h, int &s, int &c) {
   h += 4;
-  int q = (int)((sqrtf(1.0f + 0.5f * (float)h) - 1.0f) * 0.5f);
+  int q = (isqrt((h + 2) >> 1) - 1) >> 1;   // 8 q (q + 1) <= h, up to the corrections below
+  if (q < 0) q = 0;
   while (8 * (q + 1) * (q + 2) <= h) ++q;
   while (q > 0 && 8 * q * (q + 1) > h) --q;
   const int rem = h - 8 * q * (q + 1);
-  int rr = (int)((float)rem / (float)(q + 1));
-  while (rr * (q + 1) > rem) --rr;
-  while ((rr + 1) * (q + 1) <= rem) ++rr;
+  const int rr = rem / (q + 1);
   c = rem - rr * (q + 1);
   s = 16 * q + rr - 4;
 }
@@ -97,12 +122,12 @@ __device__ __forceinline__ void decode_form_chunk(int k, int m, const int *SW, i
 }
 
 // Packed index i of a form (degree <= kMaxD) -> (u, s, t).
-__device__ __forceinline__ void decode_packed(int i, int &u, int &s, int &t) {
-  int uu = (int)cbrtf(6.0f * (float)i);
+__host__ __device__ inline void decode_packed(int i, int &u, int &s, int &t) {
+  int uu = icbrt(6 * i);
   while (uu > 0 && tet(uu) > i) --uu;
   while (tet(uu + 1) <= i) ++uu;
   int rem = i - tet(uu);
-  int ss = (int)((sqrtf(8.0f * (float)rem + 1.0f) - 1.0f) * 0.5f);
+  int ss = (isqrt(8 * rem + 1) - 1) >> 1;
   while (ss > 0 && tri(ss) > rem) --ss;
   while (tri(ss + 1) <= rem) ++ss;
   u = uu;

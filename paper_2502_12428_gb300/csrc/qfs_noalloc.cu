@@ -19,8 +19,10 @@
 namespace qfs {
 namespace {
 
-// Fixed scratch per device: 64 MiB.  Bytes [0, 256) hold the work-queue counter, the check word and the work
-// counters; the rest holds the two ping-pong buffers of every persistent CTA.
+// Fixed scratch per device: 64 MiB.  Bytes [0, 256) are the control block: the work-queue counter at 0 (cleared
+// by every call), the device check word at 8 and the two work counters at 16 (both accumulate across calls until
+// qfs_read_status / qfs_read_stats take and clear them); the rest holds the two ping-pong buffers of every
+// persistent CTA.
 constexpr size_t kScratchBytes = size_t(64) << 20;
 constexpr size_t kControlBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -34,7 +36,9 @@ std::mutex g_noalloc_mu;
 
 // The device address of the array for the current device.  The array's name in host code is only a host-side
 // stand-in, so the real address comes from cudaGetSymbolAddress, once per device, with that device current.
-int scratch_for_current_device(void **out, int *sms) {
+// *fresh is set on the call that looked the address up (the first on this device).
+int scratch_for_current_device(void **out, int *sms, bool *fresh) {
+  *fresh = false;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return QFS_ERR_CUDA;
@@ -51,12 +55,43 @@ int scratch_for_current_device(void **out, int *sms) {
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) return QFS_ERR_CUDA;
     g_scratch_addr[dev] = ptr;
+    *fresh = true;
   }
   *out = g_scratch_addr[dev];
   return QFS_OK;
 }
 
 }  // namespace
+
+// Reads and clears the check word (status != nullptr) or the two work counters (stats != nullptr) that calls of
+// qfs_heights_noalloc on the current device have accumulated; reports zeros if no call has set the array up on
+// this device.  qfs_read_status and qfs_read_stats add these to their own words.  Synchronous (the caller has
+// synchronised the device).
+int noalloc_take_counters(uint32_t *status, unsigned long long *stats) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QFS_ERR_CUDA;
+  if (status) *status = 0;
+  if (stats) stats[0] = stats[1] = 0;
+  if (dev < 0 || dev >= kMaxDev) return QFS_OK;
+  void *ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    ptr = g_scratch_addr[dev];
+  }
+  if (!ptr) return QFS_OK;
+  unsigned char *base = static_cast<unsigned char *>(ptr);
+  if (status) {
+    if (cudaMemcpy(status, base + 8, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return QFS_ERR_CUDA;
+    if (cudaMemset(base + 8, 0, 4) != cudaSuccess) return QFS_ERR_CUDA;
+  }
+  if (stats) {
+    if (cudaMemcpy(stats, base + 16, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return QFS_ERR_CUDA;
+    if (cudaMemset(base + 16, 0, 16) != cudaSuccess) return QFS_ERR_CUDA;
+  }
+  // the clears are complete before a later call on any stream can add to the words
+  return cudaDeviceSynchronize() == cudaSuccess ? QFS_OK : QFS_ERR_CUDA;
+}
+
 }  // namespace qfs
 
 using namespace qfs;
@@ -77,7 +112,8 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
 
   void *scratch = nullptr;
   int sms = 0;
-  int rc = scratch_for_current_device(&scratch, &sms);
+  bool fresh = false;
+  int rc = scratch_for_current_device(&scratch, &sms, &fresh);
   if (rc) return rc;
 
   const size_t smem = smem_bytes_for(p, uses_ring_chain(QFS_FORM_DP4A, p));
@@ -111,9 +147,11 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   prm.ws = reinterpret_cast<uint32_t *>(base + kControlBytes);
   prm.ws_words = ws_words;
   prm.power_mode = QFS_POWER_CHAIN;
-  // The array keeps whatever the previous call left; only the control block must start at zero.  The chain
-  // buffers need no clearing: every word a CTA reads is written earlier in the same quartic.
-  e = cudaMemsetAsync(base, 0, kControlBytes, stream);
+  // The array keeps whatever the previous call left.  Only the work-queue counter must start at zero; the check
+  // word and the work counters accumulate until qfs_read_status / qfs_read_stats take them.  The chain buffers
+  // need no clearing: every word a CTA reads is written earlier in the same quartic.
+  // (the first call on a device clears the whole control block)
+  e = cudaMemsetAsync(base, 0, fresh ? kControlBytes : 8, stream);
   if (e != cudaSuccess) return QFS_ERR_CUDA;
   noalloc_fused_kernel<<<(int)grid, kThreads, smem, stream>>>(prm);
   e = cudaGetLastError();

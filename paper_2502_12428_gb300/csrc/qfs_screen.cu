@@ -25,7 +25,7 @@ __host__ __device__ constexpr int screen_warp_bytes(int max_p) { return 48 + 2 *
 
 // (s, t) of entry i of a slice (entries ordered by s, then t <= s).
 __device__ __forceinline__ void decode_slice_entry(int i, int &s, int &t) {
-  s = (int)((sqrtf(8.0f * (float)i + 1.0f) - 1.0f) * 0.5f);
+  s = (isqrt(8 * i + 1) - 1) >> 1;
   while (tri(s + 1) <= i) ++s;
   while (s > 0 && tri(s) > i) --s;
   t = i - tri(s);
@@ -37,9 +37,10 @@ __device__ void warp_times_f(const uint8_t *in, int m, uint8_t *out, const uint8
   const int M = m + 4;
   for (int u = 0; u <= M; ++u) {
     const int n = tri(u + 1);
-    for (int i = lane; i < n; i += 32) {
-      int s, t;
-      decode_slice_entry(i, s, t);
+    int s, t;
+    decode_slice_entry(lane, s, t);
+    for (int i = lane; i < n; i += 32, t += 32) {
+      while (t > s) t -= ++s;   // entry i = tri(s) + t: advance (s, t) by the 32 entries since the last one
       int acc = 0;
 #pragma unroll
       for (int uI = 0; uI <= 4; ++uI) {

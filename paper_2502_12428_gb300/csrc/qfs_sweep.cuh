@@ -28,8 +28,8 @@ __host__ __device__ constexpr int half_chunks_of(int s) { return (s >> 3) + 1; }
 __host__ __device__ constexpr int half_prefix(int s) { return ((s >> 3) + 1) * (4 * (s >> 3) + (s & 7)); }
 
 // Item index i -> (column s, half-chunk h).  Columns 8a .. 8a+7 hold a+1 items each, starting at 4a(a+1).
-__device__ __forceinline__ void decode_half(int i, int &s, int &h) {
-  int a = (int)((sqrtf(1.0f + (float)i) - 1.0f) * 0.5f);
+__host__ __device__ inline void decode_half(int i, int &s, int &h) {
+  int a = (isqrt(1 + i) - 1) >> 1;
   while (4 * (a + 1) * (a + 2) <= i) ++a;
   while (a > 0 && 4 * a * (a + 1) > i) --a;
   const int rem = i - 4 * a * (a + 1);

@@ -68,6 +68,7 @@ def _lib():
         L.qfs_theta_matrix.argtypes = [c_int, i64, vp, vp, vp]
         L.qfs_matmul_mod.argtypes = [c_int, c_int, c_int, c_int, vp, vp, vp, vp]
         L.qfs_poly_power.argtypes = [c_int, vp, c_int, vp, vp]
+        L.qfs_int_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
         L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -76,7 +77,7 @@ def _lib():
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
-                     "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power"):
+                     "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power", "qfs_int_peaks"):
             getattr(L, name).restype = c_int
         _LIB = L
         load_tile_table()
@@ -153,6 +154,8 @@ def heights_multi(groups, max_h=10, stream=None, form=None, engine=None, ctas_pe
         _need_cuda(out, torch.int8, "out")
         if out.numel() != coeffs.shape[0]:
             raise ValueError("out must have one entry per quartic")
+        if out.device != coeffs.device:
+            raise ValueError("out and coeffs must be on the same device")
         arr[i].p, arr[i].n = int(p), int(coeffs.shape[0])
         arr[i].coeffs, arr[i].heights_out = coeffs.data_ptr(), out.data_ptr()
         outs.append(out)
@@ -173,6 +176,10 @@ def heights_noalloc(p, coeffs, max_h=10, out=None, stream=None):
     if out is None:
         out = torch.empty(coeffs.shape[0], dtype=torch.int8, device=coeffs.device)
     _need_cuda(out, torch.int8, "out")
+    if out.numel() != coeffs.shape[0]:
+        raise ValueError("out must have one entry per quartic")
+    if out.device != coeffs.device:
+        raise ValueError("out and coeffs must be on the same device")
     rc = _lib().qfs_heights_noalloc(int(p), int(coeffs.shape[0]), coeffs.data_ptr(), int(max_h), out.data_ptr(),
                                     _stream(stream))
     _check(rc, "qfs_heights_noalloc")
@@ -287,6 +294,15 @@ def plan_prepare(p, n_hint=0):
 
 def shutdown():
     _check(_lib().qfs_shutdown(), "qfs_shutdown")
+
+
+def int_peaks():
+    """Measured integer multiply-add rates of the current device (qfs_int_peaks): dict with MACs/s of IMAD, IDP4A
+    and mma.sync s8, the SM count and the maximum SM clock in MHz."""
+    rates = (ctypes.c_double * 3)()
+    sms, khz = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib().qfs_int_peaks(rates, ctypes.byref(sms), ctypes.byref(khz)), "qfs_int_peaks")
+    return dict(imad=rates[0], dp4a=rates[1], mma_s8=rates[2], sms=sms.value, max_mhz=khz.value / 1e3)
 
 
 def read_status():

@@ -17,8 +17,51 @@ void prime_line(bool last) {
               theta_ring_words<P>(), last ? "" : ",");
 }
 
+// Mismatches of the integer index decoders against enumeration (all zero when they are right).
+void decoder_lines() {
+  long bad_sqrt = 0, bad_cbrt = 0, bad_half = 0, bad_chunk = 0, bad_packed = 0;
+  for (long k = 0; k < 32768; ++k)
+    for (long x = k * k - 1; x <= k * k + 1; ++x)
+      if (x >= 0 && x < (1l << 30)) {
+        const long r = isqrt((int)x);
+        if (r * r > x || (r + 1) * (r + 1) <= x) ++bad_sqrt;
+      }
+  for (long k = 0; k < 1024; ++k)
+    for (long x = k * k * k - 1; x <= k * k * k + 1; ++x)
+      if (x >= 0 && x < (1l << 30)) {
+        const long r = icbrt((int)x);
+        if (r * r * r > x || (r + 1) * (r + 1) * (r + 1) <= x) ++bad_cbrt;
+      }
+  // half-chunk items of columns 0 .. kMaxD + 4, chunks of a slice of columns 0 .. kMaxD + 1, packed entries
+  int i = 0;
+  for (int s = 0; s <= kMaxD + 4; ++s)
+    for (int h = 0; h < half_chunks_of(s); ++h, ++i) {
+      int s2, h2;
+      decode_half(i, s2, h2);
+      if (s2 != s || h2 != h) ++bad_half;
+    }
+  i = 0;
+  for (int s = 0; s <= kMaxD + 1; ++s)
+    for (int c = 0; c < chunks_of(s); ++c, ++i) {
+      int s2, c2;
+      decode_chunk(i, s2, c2);
+      if (s2 != s || c2 != c) ++bad_chunk;
+    }
+  i = 0;
+  for (int u = 0; u <= kMaxD; ++u)
+    for (int s = 0; s <= u; ++s)
+      for (int t = 0; t <= s; ++t, ++i) {
+        int u2, s2, t2;
+        decode_packed(i, u2, s2, t2);
+        if (u2 != u || s2 != s || t2 != t) ++bad_packed;
+      }
+  std::printf("\"decoder_mismatches\": {\"isqrt\": %ld, \"icbrt\": %ld, \"half\": %ld, \"chunk\": %ld, "
+              "\"packed\": %ld, \"packed_entries\": %d},\n", bad_sqrt, bad_cbrt, bad_half, bad_chunk, bad_packed, i);
+}
+
 int main() {
   std::printf("{\"max_d\": %d,\n", kMaxD);
+  decoder_lines();
   std::printf("\"chunks_of\": [");
   for (int s = 0; s <= kMaxD + 2; ++s) std::printf("%s%d", s ? "," : "", chunks_of(s));
   std::printf("],\n\"chunk_prefix\": [");

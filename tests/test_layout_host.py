@@ -84,3 +84,12 @@ def test_published_form_sizes(values):
     sizes = {p: (values["primes"][str(p)]["ld"], values["primes"][str(p)]["lD"]) for p in (3, 5, 7, 11)}
     assert sizes == {3: (165, 2925), 5: (969, 91881), 7: (2925, 818805), 11: (12341, 14391741)}
     assert sum(1 for _ in itertools.islice(descending_lex(4), 100)) == 35
+
+
+def test_integer_index_decoders(values):
+    # isqrt / icbrt around every square and cube, and the item, chunk and packed-index decoders over every index
+    # up to the largest degree, against enumeration: integer arithmetic only, no mismatch
+    m = values["decoder_mismatches"]
+    assert m["packed_entries"] == math.comb(values["max_d"] + 3, 3)
+    assert {k: v for k, v in m.items() if k != "packed_entries"} == {"isqrt": 0, "icbrt": 0, "half": 0, "chunk": 0,
+                                                                      "packed": 0}
