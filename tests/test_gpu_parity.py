@@ -116,64 +116,6 @@ def test_route_a_subset_p5(qfs):
     assert np.array_equal(gpu_heights(qfs, 5, f), want)
 
 
-# ------------------------------------------------------------------------------------- full sizes, sampled
-def sampled_check(qfs, p, f, got, n_uniform=1500, seed=0):
-    n = f.shape[0]
-    rng = np.random.default_rng(seed)
-    idx = set(rng.choice(n, size=min(n_uniform, n), replace=False).tolist())
-    idx |= set(np.nonzero((got >= 3) | (got == 0))[0][:4000].tolist())  # every rare outcome up to a cap
-    idx = np.array(sorted(idx))
-    want = oracle.heights(p, f[idx])
-    assert np.array_equal(got[idx], want)
-    return idx.size
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("cfg", [2, 4])
-def test_full_size_dense(qfs, cfg):
-    (p, n, kind), = inputs.CONFIG_SIZES[cfg]
-    f = inputs.dense(p, n, inputs.config_seed(cfg))
-    ft = dev_tensor(f)
-    got = {form: qfs.heights(p, ft, form=form).cpu().numpy() for form in CORE_FORMS}
-    assert np.array_equal(got["int32"], got["dp4a"])
-    assert np.array_equal(got["int8tc"], got["dp4a"])
-    h = got["dp4a"]
-    assert h.min() >= 0 and h.max() <= 10
-    checked = sampled_check(qfs, p, f, h, seed=cfg)
-    assert checked > 1000
-    # the h >= 2 fraction sits near the 1/p of the paper's heuristic (Sec. 7), wide band
-    frac = float((h != 1).mean())
-    assert abs(frac - 1 / p) < 0.05
-
-
-@pytest.mark.slow
-def test_full_size_sparse_p5(qfs):
-    (p, n, kind), = inputs.CONFIG_SIZES[3]
-    f = inputs.sparse(p, n, inputs.config_seed(3))
-    h = gpu_heights(qfs, p, f)
-    assert h.min() >= 0 and h.max() <= 10
-    sampled_check(qfs, p, f, h, n_uniform=3000, seed=3)
-
-
-@pytest.mark.slow
-def test_full_size_mixed_sampled(qfs):
-    # the mixed-prime workload at full size in one launch (131,072 quartics at p = 5 and at p = 7, 4,096 at p = 11,
-    # each followed by its PGL_4 image): every group sampled against the oracle, every image with its row's height
-    seed = inputs.config_seed(5)
-    groups, rows = [], []
-    for p, n, kind in inputs.CONFIG_SIZES[5]:
-        f = inputs.dense(p, n, seed + p)
-        A = inputs.pgl4_matrices(p, n, seed + 100 + p)
-        both = np.concatenate([f, inputs.substitute(f, A, p)])
-        groups.append((p, dev_tensor(both), None))
-        rows.append((p, n, both))
-    outs = [o.cpu().numpy() for o in qfs.heights_multi(groups)]
-    for (p, n, both), out in zip(rows, outs):
-        assert out.min() >= 0 and out.max() <= 10
-        assert np.array_equal(out[:n], out[n:])
-        sampled_check(qfs, p, both, out, n_uniform=1500 if p < 11 else 200, seed=p)
-
-
 # ------------------------------------------------------------------------------------- mixed primes in one launch
 def test_multi_group_mixed_and_pgl4(qfs):
     groups, wants, pairs = [], [], []
