@@ -21,7 +21,7 @@ _SOURCES = ["hpoly.c", "route_a.c", "route_r.c", "batch.c"]
 _lib = None
 
 __all__ = ["build", "lib", "load", "Oracle", "monomial_count", "height_a", "height_r", "heights", "delta1", "split_u",
-           "stage_arrays_a", "stage_arrays_r", "theta_matrix", "matmul_mod", "poly_power",
+           "stage_arrays_a", "stage_arrays_r", "stage_arrays_fchain", "theta_matrix", "matmul_mod", "poly_power",
            "form_monomials", "ROUTE_A", "ROUTE_R"]
 
 ROUTE_A = 0
@@ -69,6 +69,8 @@ def load(path):
         L.qfs_oracle_delta1.restype = ctypes.c_int
         L.qfs_oracle_split_u.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p]
         L.qfs_oracle_split_u.restype = ctypes.c_int
+        L.qfs_oracle_stages_fchain.argtypes = [ctypes.c_int, u8p, i32p, i32p, i32p]
+        L.qfs_oracle_stages_fchain.restype = ctypes.c_int
     return L
 
 
@@ -139,6 +141,25 @@ def stage_arrays_a(p, f, max_h=10, lift_signed=False):
         n_rows = (h - 1) if h >= 2 else _rows_until_zero_or_end(iters, p, max_h)
         out["iters"] = iters[:n_rows]
     return out
+
+
+def stage_arrays_fchain(p, f):
+    """g = f^(p-1) mod p and, past the height-1 test, D = lift(f)^(p(p-1)) mod p^2 (the same array as route A's
+    lift(g)^p, formed by products with f's 35 terms) and Delta_1(g) by Algorithm 1's subtraction and division.
+    Returns dict(h1, g, D, delta): h1 = True if the height is 1 (then D and delta are None)."""
+    f = _quartic(f)
+    ld = monomial_count(4 * (p - 1))
+    lD = monomial_count(4 * p * (p - 1))
+    g = np.zeros(ld, np.int32)
+    D = np.zeros(lD, np.int32)
+    delta = np.zeros(lD, np.int32)
+    rc = lib().qfs_oracle_stages_fchain(p, _ptr(f, ctypes.c_uint8), _ptr(g, ctypes.c_int32), _ptr(D, ctypes.c_int32),
+                                        _ptr(delta, ctypes.c_int32))
+    if rc == -2:
+        raise ArithmeticError("division by p in Algorithm 1 is not exact")
+    if rc < 0:
+        raise ValueError(f"oracle failure {rc}")
+    return dict(h1=rc == 1, g=g, D=None if rc == 1 else D, delta=None if rc == 1 else delta)
 
 
 def stage_arrays_r(p, f, max_h=10):

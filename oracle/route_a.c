@@ -25,6 +25,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The end of Algorithm 1, given D = lift^p mod p^2 for the lift `lift` of g: subtract t^p for every term t of the
+   lift, divide by p and read the result mod p into Delta.  Consumes D and lift.  Returns 0, -2 if a division is not
+   exact, or -1 on allocation failure. */
+static int alg1_subtract_divide(int p, hpoly *lift, hpoly *D, hpoly *Delta);
+
 /* Algorithm 1 on a homogeneous g of degree deg with coefficients in [0,p).  Fills D (= lift^p mod p^2, before the
    subtraction) and Delta (mod p), both of degree p*deg.  Returns 0, or -2 if some coefficient of D - S is not
    divisible by p (impossible by the Proposition; reported rather than ignored), or -1 on allocation failure. */
@@ -56,6 +61,13 @@ static int delta1_alg1(int p, const hpoly *g, int lift_signed, hpoly *D_out, hpo
     if (hpoly_init(D_out, D.deg)) { hpoly_free(&D); hpoly_free(&lift); return -1; }
     memcpy(D_out->c, D.c, (size_t)D.side * D.side * D.side * sizeof(int64_t));
   }
+  return alg1_subtract_divide(p, &lift, &D, Delta);
+}
+
+static int alg1_subtract_divide(int p, hpoly *lift_in, hpoly *D_in, hpoly *Delta) {
+  const int64_t p2 = (int64_t)p * p;
+  hpoly lift = *lift_in, D = *D_in;
+  const hpoly *g = &lift;
   /* D <- D - t^p for every term t = c x^J of the lift: t^p = c^p x^(pJ). */
   for (int e1 = 0; e1 <= g->deg; e1++)
     for (int e2 = 0; e1 + e2 <= g->deg; e2++)
@@ -166,6 +178,47 @@ int qfs_oracle_split_u(int p, int deg, const int32_t *P_desc, int32_t *out) {
   int d = U.deg;
   hpoly_free(&U);
   return d;
+}
+
+/* Stage arrays of Algorithms 1 and 3 for one quartic with D formed as lift(f)^(p(p-1)) mod p^2, one product by
+   the lift of f at a time, instead of lift(g)^p by products of the lift of g = f^(p-1) (route A).  The two are the
+   same array: termwise lifts agree mod p, and (c + p b)^p = c^p mod p^2 carries that to the p-th power, so
+   lift(g)^p = (lift(f)^(p-1) + p B)^p = lift(f)^(p(p-1)) mod p^2.  Products by the 35 terms of f keep the p = 11 and
+   p = 13 arrays within a test's time, where products by the C(4p-1,3) terms of g do not.  Outputs as for
+   qfs_oracle_height_a: g_out = f^(p-1) mod p, then (if the witness coefficient is zero) D_out and delta_out.
+   Returns 1 if the witness coefficient is nonzero, 0 if D and Delta were written, -1 for a coefficient >= p, -2 if
+   a division by p was not exact, -3 on allocation failure. */
+int qfs_oracle_stages_fchain(int p, const uint8_t *f35, int32_t *g_out, int32_t *D_out, int32_t *delta_out) {
+  const int64_t p2 = (int64_t)p * p;
+  hpoly f, g, t;
+  int rc = load_quartic(p, f35, &f);
+  if (rc) return rc;
+  if (hpoly_init(&g, 0)) { hpoly_free(&f); return -3; }
+  g.c[0] = 1;
+  for (int k = 1; k <= p - 1; k++) {
+    if (hpoly_mul_mod(&t, &g, &f, p)) { hpoly_free(&g); hpoly_free(&f); return -3; }
+    hpoly_free(&g);
+    g = t;
+  }
+  if (g_out) hpoly_to_desc_lex(&g, g_out);
+  if (witness_coeff(p, &g) != 0) { hpoly_free(&g); hpoly_free(&f); return 1; }
+  /* D <- lift(f)^(p(p-1)) mod p^2 (f's coefficients are already in [0, p)) */
+  hpoly D;
+  if (hpoly_init(&D, 0)) { hpoly_free(&g); hpoly_free(&f); return -3; }
+  D.c[0] = 1;
+  for (int k = 1; k <= p * (p - 1); k++) {
+    if (hpoly_mul_mod(&t, &D, &f, p2)) { hpoly_free(&D); hpoly_free(&g); hpoly_free(&f); return -3; }
+    hpoly_free(&D);
+    D = t;
+  }
+  hpoly_free(&f);
+  if (D_out) hpoly_to_desc_lex(&D, D_out);
+  hpoly Delta;
+  rc = alg1_subtract_divide(p, &g, &D, &Delta);   /* the lift of g is g itself: coefficients in [0, p) */
+  if (rc == -1) return -3;
+  if (delta_out) hpoly_to_desc_lex(&Delta, delta_out);
+  hpoly_free(&Delta);
+  return rc == -2 ? -2 : 0;
 }
 
 /* Algorithm 3.  Returns the height 1..max_h, 0 for infinity / not found by max_h, -1 for a coefficient >= p,

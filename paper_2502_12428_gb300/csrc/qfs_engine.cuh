@@ -488,11 +488,14 @@ inline size_t theta_guarded_words(int p) {
   return (size_t)host_sw(D + 1) + (size_t)theta_gsw_extra(D + 1);
 }
 
-// Workspace buffer stride (see qfs_common.cuh): a padded degree-D form, or theta's guarded copy of Delta, which is
-// larger (p = 7 streams Delta through shared memory instead and needs no copy).
+// Words of Delta in residue-class order (theta at p <= 7): every class of degree d - k starts on a 16-byte boundary.
+inline size_t theta_class_words(int p);
+
+// Workspace buffer stride (see qfs_common.cuh): a padded degree-D form, and room for theta's copy of Delta: the
+// residue-class order at p <= 7, the guarded copy at p >= 11 (which is larger than the padded form).
 inline size_t workspace_stride_words(int p) {
   const size_t padded = (size_t)padded_words(4 * p * (p - 1));
-  return (p == 7 ? padded : std::max(padded, theta_guarded_words(p))) + kGuardWords;
+  return std::max(padded, p <= 7 ? theta_class_words(p) : theta_guarded_words(p)) + kGuardWords;
 }
 
 // Reversed g columns: column (u_c, s_c) holds g[u_c, s_c, s_c - j] at byte j (j <= s_c), zero-padded to whole words.
@@ -505,27 +508,62 @@ __host__ __device__ constexpr int theta_r_words() {
   for (int u = 0; u <= 4 * (P - 1); ++u) r += rcolw(u + 1);
   return r;
 }
-// Theta at p = 7 streams Delta slice by slice through shared memory (two guarded slice slots): the guarded copies
-// of all CTAs (1.7 MB each) would not stay in L2.  At p <= 5 they do (0.3 MB each), and the per-output gather from
-// the guarded copy in global memory is faster; at p >= 11 a slice of Delta does not fit twice in shared memory.
+// Theta runs by residue classes at p <= 7 (theta_poly below) and gathers from the guarded copy at p >= 11, whose
+// padded cube of one class would not fit in shared memory.
 template <int P>
-__host__ __device__ constexpr bool theta_streams() { return P == 7; }
-// a slice slot: columns 0 .. D with the guards of the guarded layout
+__host__ __device__ constexpr bool theta_by_classes() { return P <= 7; }
+
+// Residue classes of theta at p <= 7.  Writing c = p c' + rho with rho in [0,p)^4 (per exponent) turns
+//   theta(g)[r] = sum_c Delta[p r + (p-1)1 - c] g[c]
+// into a sum of products of forms: the exponent p (r - c') + (p-1)1 - rho is non-negative exactly when c' <= r, so
+//   theta(g) = sum_rho Delta_sigma * g_rho,   Delta_sigma[e] = Delta[p e + sigma], g_rho[c'] = g[p c' + rho],
+// with sigma = (p-1)1 - rho.  |rho| = d - p k with k = deg g_rho in {0, .., 3}, and deg Delta_sigma = d - k; the p^3
+// classes hold every coefficient of g once and every coefficient of Delta once, and the MACs add up to the theta
+// matrix's nonzeros.  Each class is a product with a kernel of at most 20 taps, computed on a zero-padded cube of
+// Delta_sigma in shared memory, so no term needs a bounds check.
 template <int P>
-__host__ __device__ constexpr int theta_slot_words() { return kThetaGuardWords * (4 * P * (P - 1) + 2) + colw(4 * P * (P - 1) + 1); }
-// shared-memory words theta uses in the ring: reversed g columns and their slice table; when streaming also two
-// slice slots, int32 accumulators, the chunk-to-slot table and the unpacked output coordinates
-// slice slots of the streamed theta: a deeper ring where slots are small (prefetch distance slots - 1)
-template <int P>
-__host__ __device__ constexpr int theta_nslots() { return P <= 5 ? 4 : 2; }
-// word offset of the slice slots in the ring (16-byte aligned for cp.async)
-template <int P>
-__host__ __device__ constexpr int theta_slots_off() { return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3; }
+struct Poly {
+  static constexpr int d = 4 * (P - 1), ld = tet(d + 1);
+  static constexpr int C = d + 4;                       // cube side: coordinates -3 .. d
+  static constexpr int CB = (C * C * C + 15) & ~15;     // bytes of one cube
+  static constexpr int NCLS = P * P * P;
+  static constexpr int NOUT = (ld + kThreads - 1) / kThreads;   // outputs per thread
+  // ring layout (bytes): two cubes, the taps of every class (ld bytes), the g index of every tap (ld x u16), the
+  // cube address of every packed index of B_d (ld x u16), the class records (NCLS x 16 bytes), per-k counters
+  static constexpr int taps_off = 2 * CB;
+  static constexpr int tapsrc_off = taps_off + ((ld + 15) & ~15);
+  static constexpr int cubeaddr_off = tapsrc_off + ((2 * ld + 15) & ~15);
+  static constexpr int cls_off = cubeaddr_off + ((2 * ld + 15) & ~15);
+  static constexpr int cnt_off = cls_off + 16 * NCLS;
+  static constexpr int bytes = cnt_off + 16;
+};
+
+// Classes of degree k (kernel degree) in residue-class order: rho in [0,p)^4 with |rho| = d - p k.
+__host__ __device__ constexpr int poly_count(int p, int k) {
+  int n = 0;
+  for (int r1 = 0; r1 < p; ++r1)
+    for (int r2 = 0; r2 < p; ++r2)
+      for (int r3 = 0; r3 < p; ++r3)
+        for (int r4 = 0; r4 < p; ++r4)
+          if (r1 + r2 + r3 + r4 == 4 * (p - 1) - p * k) ++n;
+  return n;
+}
+// bytes of one class of kernel degree k in global memory: C(d - k + 3, 3), rounded up to 16
+__host__ __device__ constexpr int poly_class_bytes(int p, int k) { return (tet(4 * (p - 1) - k + 1) + 15) & ~15; }
+
+inline size_t theta_class_words(int p) {
+  size_t b = 0;
+  for (int k = 0; k <= 3; ++k) b += (size_t)poly_count(p, k) * poly_class_bytes(p, k);
+  return b / 4;
+}
+
 template <int P>
 __host__ __device__ constexpr int theta_ring_words() {
-  constexpr int d = 4 * (P - 1), D = 4 * P * (P - 1), ld = tet(d + 1);
-  return theta_slots_off<P>() +
-         (theta_streams<P>() ? theta_nslots<P>() * theta_slot_words<P>() + ld + chunk_prefix(D + 1) + ld + D + 1 : 0);
+  if constexpr (theta_by_classes<P>()) {
+    return (Poly<P>::bytes + 3) / 4;
+  } else {
+    return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3;   // reversed g columns and their slice table
+  }
 }
 
 __host__ __device__ inline int theta_ring_words_for(int p) {
@@ -596,7 +634,7 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
   bool any = false;
   for (int r = tid; r < Pr::ld; r += nthreads) {
     int ur, sr, tr;
-    decode_packed(r, ur, sr, tr);
+    decode_packed(r, ur, sr, tr, d);
     const int Ue = P * ur + 3 * (P - 1), Se = P * sr + 2 * (P - 1), Te = P * tr + (P - 1);
     const int uc_lo = max(0, Ue - D), uc_hi = min(d, Ue);
     unsigned acc = 0;
@@ -635,168 +673,219 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
   return __syncthreads_or(any ? 1 : 0) != 0;
 }
 
-// Up to four g columns s_c = sc0 .. sc1 of a streamed theta round, all of NW words (sc0 / 4 == sc1 / 4), for the
-// output r = (u_r, s_r, t_r) of this lane: each column s_c inside the lane's range [lo, hi] adds the lane's Delta
-// window (NW + 1 words of the guarded slot, shifted to the window's first byte) against the NW words of g's
-// reversed column s_c, which are the same for every lane.  ebase = p s_r + 2(p-1), so the Delta column is
-// e_s = ebase - s_c; tbase = p t_r + (p-1), the window's last byte in that column.  All loads of the four columns
-// are issued before the first product.
-template <int P, int NW>
-__device__ __forceinline__ unsigned theta_seg(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rb,
-                                              const int *__restrict__ gofs, int sc0, int sc1, int lo, int hi,
-                                              int ebase, int tbase, unsigned a) {
-  uint32_t dv[4][NW + 1], rv[4][NW];
-  unsigned sh[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int sc = sc0 + j;
-    const bool in = sc <= sc1;
-    const bool on = in && sc >= lo && sc <= hi;
-    const int byte = on ? gofs[ebase - sc] + tbase - sc : 0;
-    sh[j] = 8u * (unsigned)(byte & 3);
-    const uint32_t *dw = slot + (byte >> 2);
-#pragma unroll
-    for (int k = 0; k <= NW; ++k) dv[j][k] = on ? dw[k] : 0u;
-    const uint32_t *rw = Rb + rcolw(sc);
-#pragma unroll
-    for (int k = 0; k < NW; ++k) rv[j][k] = in ? rw[k] : 0u;
+// Class records of theta_poly (ring, Poly<P>::cls_off): x = byte offset of Delta_sigma in the class-ordered copy,
+// y = offset of g_rho's taps in the tap arrays, z = k | Su << 8 | Ss << 16 | St << 24 where (Su, Ss, St) is sigma in
+// (u, s, t) coordinates (Delta_sigma[u', s', t'] = Delta[p u' + Su, p s' + Ss, p t' + St]).  Classes are ordered by
+// k, which theta_poly's cube clearing relies on; inside one k the order is whatever the atomic counters hand out.
+// Also fills the tap sources (the packed index in B_d of g_rho's tap c', in the packed order of c' in B_k) and the
+// cube address of every packed index of B_d.  Ends with a barrier.
+template <int P>
+__device__ __forceinline__ void poly_tables(unsigned char *ring) {
+  using Q = Poly<P>;
+  constexpr int d = Q::d, C = Q::C;
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  uint16_t *tapsrc = reinterpret_cast<uint16_t *>(ring + Q::tapsrc_off);
+  uint16_t *cubeaddr = reinterpret_cast<uint16_t *>(ring + Q::cubeaddr_off);
+  int4 *cls = reinterpret_cast<int4 *>(ring + Q::cls_off);
+  int *cnt = reinterpret_cast<int *>(ring + Q::cnt_off);
+  if (tid < 4) cnt[tid] = 0;
+  for (int i = tid; i < Q::ld; i += nthreads) {
+    int u, s, t;
+    decode_packed(i, u, s, t, d);
+    cubeaddr[i] = (uint16_t)((u + 3) * C * C + (s + 3) * C + t + 3);
   }
+  __syncthreads();
+  constexpr int NQ = (Q::NCLS + kThreads - 1) / kThreads;
+  int slot[NQ];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int q = 0; q < NQ; ++q) {
+    const int x = tid + kThreads * q;
+    slot[q] = -1;
+    if (x < Q::NCLS) {
+      const int r2 = x % P, r3 = (x / P) % P, r4 = x / (P * P);
+      const int r1 = ((d - r2 - r3 - r4) % P + P) % P;
+      const int k = (d - (r1 + r2 + r3 + r4)) / P;
+      slot[q] = atomicAdd(&cnt[k], 1);
+    }
+  }
+  __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NW; ++k) a = __dp4a(__funnelshift_r(dv[j][k], dv[j][k + 1], sh[j]), rv[j][k], a);
-  return a;
+  for (int q = 0; q < NQ; ++q) {
+    const int x = tid + kThreads * q;
+    if (slot[q] < 0) continue;
+    const int r2 = x % P, r3 = (x / P) % P, r4 = x / (P * P);
+    const int r1 = ((d - r2 - r3 - r4) % P + P) % P;
+    const int k = (d - (r1 + r2 + r3 + r4)) / P;
+    int j = slot[q], goff = 0, toff = 0;
+    for (int kk = 0; kk < k; ++kk) {
+      j += cnt[kk];
+      goff += cnt[kk] * poly_class_bytes(P, kk);
+      toff += cnt[kk] * tet(kk + 1);
+    }
+    goff += slot[q] * poly_class_bytes(P, k);
+    toff += slot[q] * tet(k + 1);
+    const int s2 = P - 1 - r2, s3 = P - 1 - r3, s4 = P - 1 - r4;
+    cls[j] = make_int4(goff, toff, k | ((s2 + s3 + s4) << 8) | ((s3 + s4) << 16) | (s4 << 24), 0);
+    // taps: g[p c' + rho] for c' = (uc, sc, tc) in B_k, rho = (r2 + r3 + r4, r3 + r4, r4) in (u, s, t)
+    int i = 0;
+    for (int uc = 0; uc <= k; ++uc)
+      for (int sc = 0; sc <= uc; ++sc)
+        for (int tc = 0; tc <= sc; ++tc, ++i)
+          tapsrc[toff + i] = (uint16_t)(tet(P * uc + r2 + r3 + r4) + tri(P * sc + r3 + r4) + P * tc + r4);
+  }
+  __syncthreads();
 }
 
-// One theta step with Delta (padded, degree D, global memory) streamed through shared memory (p = 7).  Round e_u
-// copies slice e_u into a guarded slot (16-byte cp.async, double buffered) and serves every output slice u_r whose
-// g slice u_c = p u_r + 3(p-1) - e_u exists, in blocks of 32 consecutive outputs (one per lane) that sum over the
-// g columns in registers; each round's sums go to shared int32 accumulators.  Every Delta byte is read from global
-// memory once per step.  Returns whether some output is nonzero (same value in every thread).
+// Padded Delta (degree D) -> class order: class j holds Delta_sigma in packed order of B_{d-k} at byte offset
+// cls[j].x of `dc`.  One thread per destination word (four consecutive packed indices of one class); the bytes are
+// read from the padded layout at (p u' + Su, p s' + Ss, p t' + St).  Classes of the same (sigma2, sigma3 + sigma4)
+// read the same Delta columns.  The caller synchronises the CTA afterwards.
 template <int P>
-__device__ __noinline__ bool theta_stream(const uint32_t *__restrict__ delta, const Smem &sm,
-                                          const uint8_t *__restrict__ g, uint8_t *__restrict__ gn, uint32_t *ring) {
-  static_assert(P <= 7, "g columns of at most 7 words");
-  using Pr = Prime<P>;
-  constexpr int d = Pr::d, D = Pr::D, ld = Pr::ld;
-  constexpr int SLOT = theta_slot_words<P>();
-  const int tid = threadIdx.x, nthreads = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
-  uint32_t *R = ring;
-  int *RSW = reinterpret_cast<int *>(ring + theta_r_words<P>());
-  constexpr int NS = theta_nslots<P>();
-  uint32_t *slots = ring + theta_slots_off<P>();                        // NS x SLOT, 16-byte aligned
-  int *acc = reinterpret_cast<int *>(slots + NS * SLOT);
-  int *ctab = acc + ld;                                                 // flat chunk of a slice -> slot word
-  uint32_t *rst = reinterpret_cast<uint32_t *>(ctab + chunk_prefix(D + 1));   // output r -> ur | sr << 8 | tr << 16
-  int *gofs = reinterpret_cast<int *>(rst + ld);                        // column e_s -> byte offset in a slot
-  for (int es = tid; es <= D; es += nthreads) gofs[es] = 4 * (kThetaGuardWords * (es + 1) + colw(es));
-  if (tid == 0) {
-    int a = 0;
-    for (int u = 0; u <= d + 1; ++u) { RSW[u] = a; a += rcolw(u + 1); }
-  }
-  for (int i = tid; i < NS * SLOT; i += nthreads) slots[i] = 0u;
-  for (int i = tid; i < ld; i += nthreads) {
-    acc[i] = 0;
-    int u, s, t;
-    decode_packed(i, u, s, t);
-    rst[i] = (uint32_t)u | ((uint32_t)s << 8) | ((uint32_t)t << 16);
-  }
-  for (int k = tid; k < chunk_prefix(D + 1); k += nthreads) {
-    int es, c;
-    decode_chunk(k, es, c);
-    ctab[k] = kThetaGuardWords * (es + 1) + colw(es) + 4 * c;
-  }
-  __syncthreads();
-  for (int i = tid; i < theta_r_words<P>(); i += nthreads) {
-    int u = 0;
-    while (RSW[u + 1] <= i) ++u;
-    const int rem = i - RSW[u];
-    int sc = 0;
-    while (rcolw(sc + 1) <= rem) ++sc;
-    const int k = rem - rcolw(sc);
-    const uint8_t *gcol = g + tet(u) + tri(sc);
-    uint32_t w = 0;
+__device__ __forceinline__ void delta_to_classes(const uint32_t *__restrict__ delta, uint32_t *__restrict__ dc,
+                                                 const Smem &sm, const unsigned char *ring) {
+  using Q = Poly<P>;
+  constexpr int C = Q::C;
+  const uint16_t *cubeaddr = reinterpret_cast<const uint16_t *>(ring + Q::cubeaddr_off);
+  const int4 *cls = reinterpret_cast<const int4 *>(ring + Q::cls_off);
+  const uint8_t *db = reinterpret_cast<const uint8_t *>(delta);
+  for (int j = 0; j < Q::NCLS; ++j) {
+    const int4 c = cls[j];
+    const int k = c.z & 255, Su = (c.z >> 8) & 255, Ss = (c.z >> 16) & 255, St = (c.z >> 24) & 255;
+    const int len = tet(Q::d - k + 1);
+    for (int w = threadIdx.x; 4 * w < len; w += blockDim.x) {
+      uint32_t word = 0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = 4 * k + b;
-      if (j <= sc) w |= (uint32_t)gcol[sc - j] << (8 * b);
-    }
-    R[i] = w;
-  }
-  auto fetch = [&](int eu, int buf) {
-    uint32_t *dst = slots + buf * SLOT;
-    const uint32_t *src = delta + sm.SW[eu];
-    const int n = chunk_prefix(eu + 1);
-    for (int k = tid; k < n; k += nthreads) cp_async16(dst + ctab[k], src + 4 * k, true);
-  };
-  // slices 0 .. NS-2 in flight; round e_u waits for its own slice, then refills the slot round e_u - 1 used
-  for (int e = 0; e < NS - 1; ++e) {
-    if (e <= D) fetch(e, e);
-    cp_async_commit();
-  }
-  for (int eu = 0; eu <= D; ++eu) {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));
-    __syncthreads();   // slot eu % NS is complete for every thread; slot (eu - 1) % NS is no longer read
-    if (eu + NS - 1 <= D) fetch(eu + NS - 1, (eu + NS - 1) % NS);
-    cp_async_commit();
-    const uint32_t *slot = slots + (eu % NS) * SLOT;
-    // output slices with u_c = p u_r + 3(p-1) - e_u in [0, d]
-    const int base = eu - 3 * (P - 1);
-    const int ur_lo = max(0, (base + P - 1) / P);
-    const int ur_hi = min(d, base + d >= 0 ? (base + d) / P : -1);
-    if (ur_lo > ur_hi) continue;
-    // blocks of 32 consecutive outputs of a slice u_r, one warp each (lane = output): a lane sums, over every g
-    // column s_c whose Delta column e_s = p s_r + 2(p-1) - s_c lies in slice e_u, in registers, and adds the total
-    // to its output once per round; the warp runs the union of its lanes' column ranges, four columns at a time
-    int nblocks = 0;
-    for (int ur = ur_lo; ur <= ur_hi; ++ur) nblocks += (tri(ur + 1) + 31) >> 5;
-    for (int blk = warp; blk < nblocks; blk += nwarps) {
-      int ur = ur_lo, b = blk;
-      for (;;) {
-        const int nb = (tri(ur + 1) + 31) >> 5;
-        if (b < nb) break;
-        b -= nb;
-        ++ur;
-      }
-      const int uc = P * ur - base;   // in [0, d] for ur in [ur_lo, ur_hi]
-      const int i = 32 * b + lane;
-      const bool act = i < tri(ur + 1);
-      const int r = tet(ur) + i;
-      int lo = 1 << 30, hi = -1, ebase = 0, tbase = 0;
-      if (act) {
-        const uint32_t x = rst[r];
-        ebase = P * (int)((x >> 8) & 255u) + 2 * (P - 1);
-        tbase = P * (int)(x >> 16) + (P - 1);
-        lo = max(0, ebase - eu);   // e_s <= e_u
-        hi = min(uc, ebase);       // e_s >= 0
-      }
-      const int wlo = __reduce_min_sync(0xffffffffu, lo), whi = __reduce_max_sync(0xffffffffu, hi);
-      if (wlo > whi) continue;
-      const uint32_t *Rb = R + RSW[uc];
-      unsigned a = 0;
-      for (int q = wlo >> 2; q <= (whi >> 2); ++q) {
-        const int sc0 = max(wlo, 4 * q), sc1 = min(whi, 4 * q + 3);
-        switch (q) {   // words of g's reversed column: s_c / 4 + 1 <= p
-          case 0: a = theta_seg<P, 1>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          case 1: a = theta_seg<P, 2>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          case 2: a = theta_seg<P, 3>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          case 3: a = theta_seg<P, 4>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          case 4: a = theta_seg<P, 5>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          case 5: a = theta_seg<P, 6>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
-          default: a = theta_seg<P, 7>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * w + b;
+        if (i < len) {
+          // (u', s', t') of packed index i from its cube address
+          const int a = cubeaddr[i];
+          const int u = a / (C * C) - 3, s = (a / C) % C - 3, t = a % C - 3;
+          const int U = P * u + Su, S = P * s + Ss, T = P * t + St;
+          word |= (uint32_t)db[4 * (sm.SW[U] + colw(S)) + T] << (8 * b);
         }
       }
-      if (act && a != 0u) atomicAdd(acc + r, (int)a);
+      dc[c.x / 4 + w] = word;
     }
   }
-  cp_async_wait_all();
+}
+
+// Products of one class: acc[o] += sum over the taps c' in B_K of g_rho[c'] Delta_sigma[r_o - c'], reading
+// Delta_sigma from the zero-padded cube at a[o] - offset(c').
+template <int P, int K>
+__device__ __forceinline__ void poly_macs(const uint8_t *cube, const uint8_t *tp, const int (&a)[Poly<P>::NOUT],
+                                          int (&acc)[Poly<P>::NOUT]) {
+  constexpr int C = Poly<P>::C;
+#pragma unroll
+  for (int uc = 0; uc <= K; ++uc)
+#pragma unroll
+    for (int sc = 0; sc <= uc; ++sc)
+#pragma unroll
+      for (int tc = 0; tc <= sc; ++tc) {
+        const int tv = tp[tet(uc) + tri(sc) + tc];
+        const int off = uc * C * C + sc * C + tc;
+#pragma unroll
+        for (int o = 0; o < Poly<P>::NOUT; ++o) acc[o] += tv * (int)cube[a[o] - off];
+      }
+}
+
+// One theta step by residue classes (p <= 7): g (shared, packed) -> gn.  `dc` holds Delta in class order
+// (delta_to_classes) and poly_tables has run.  Classes stream through two cubes in shared memory: class j + 1's
+// words are loaded while class j is multiplied, then scattered into the other cube, with one barrier per class.
+// Cube positions outside B_d are zero from the start; when the degree d - k of the classes drops, the cube's slab
+// of the old degree is cleared, so each cube always holds zeros outside its current class's cone.  Returns whether
+// some output is nonzero (same value in every thread).
+template <int P>
+__device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const uint8_t *__restrict__ g,
+                                        uint8_t *__restrict__ gn, unsigned char *ring) {
+  using Q = Poly<P>;
+  // every thread of the CTA (kThreads of them) owns NOUT outputs and NWT words of a class
+  constexpr int d = Q::d, ld = Q::ld, C = Q::C, NOUT = Q::NOUT;
+  constexpr int NW = (ld + 3) / 4;                           // words of the largest class
+  constexpr int NWT = (NW + kThreads - 1) / kThreads;        // words per thread
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  uint8_t *cube0 = ring;
+  uint8_t *taps = ring + Q::taps_off;
+  const uint16_t *tapsrc = reinterpret_cast<const uint16_t *>(ring + Q::tapsrc_off);
+  const uint16_t *cubeaddr = reinterpret_cast<const uint16_t *>(ring + Q::cubeaddr_off);
+  const int4 *cls = reinterpret_cast<const int4 *>(ring + Q::cls_off);
+  // taps of every class in class order, and both cubes cleared
+  for (int i = tid; i < ld; i += nthreads) taps[i] = g[tapsrc[i]];
+  for (int i = tid; i < 2 * Q::CB / 16; i += nthreads) reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
+  // output addresses: r_o = tid + kThreads o; threads past B_d read the (zero) cube at output (0, 0, 0)
+  int a[NOUT], acc[NOUT];
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) {
+    const int r = tid + kThreads * o;
+    a[o] = r < ld ? (int)cubeaddr[r] : 3 * C * C + 3 * C + 3;
+    acc[o] = 0;
+  }
+  // class 0 into cube 0
+  int degb[2] = {d, d};   // degree of the cone each cube was last filled with (uniform)
+  {
+    const int4 c = cls[0];
+    const int len = tet(d - (c.z & 255) + 1);
+    for (int w = tid; 4 * w < len; w += nthreads) {
+      const uint32_t word = dc[c.x / 4 + w];
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * w + b < len) cube0[cubeaddr[4 * w + b]] = (uint8_t)(word >> (8 * b));
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < Q::NCLS; ++j) {
+    const int4 c = cls[j];
+    const int k = c.z & 255;
+    uint8_t *cube = cube0 + (j & 1) * Q::CB;
+    uint8_t *next = cube0 + ((j + 1) & 1) * Q::CB;
+    // class j + 1's words in flight while class j is multiplied
+    uint32_t pre[NWT];
+    int nlen = 0, nk = 0;
+    if (j + 1 < Q::NCLS) {
+      const int4 cn = cls[j + 1];
+      nk = cn.z & 255;
+      nlen = tet(d - nk + 1);
+#pragma unroll
+      for (int q = 0; q < NWT; ++q) {
+        const int w = tid + kThreads * q;
+        pre[q] = 4 * w < nlen ? dc[cn.x / 4 + w] : 0u;
+      }
+    }
+    const uint8_t *tp = taps + c.y;
+    switch (k) {
+      case 0: poly_macs<P, 0>(cube, tp, a, acc); break;
+      case 1: poly_macs<P, 1>(cube, tp, a, acc); break;
+      case 2: poly_macs<P, 2>(cube, tp, a, acc); break;
+      default: poly_macs<P, 3>(cube, tp, a, acc); break;
+    }
+    if (j + 1 < Q::NCLS) {
+      // the other cube: clear the slab its previous class left beyond the new degree, then scatter class j + 1
+      const int b = (j + 1) & 1;
+      const int nd = d - nk;
+      if (degb[b] > nd) {
+        for (int i = tet(nd + 1) + tid; i < tet(degb[b] + 1); i += nthreads) next[cubeaddr[i]] = 0;
+        degb[b] = nd;
+      }
+#pragma unroll
+      for (int q = 0; q < NWT; ++q) {
+        const int w = tid + kThreads * q;
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb)
+          if (4 * w + bb < nlen) next[cubeaddr[4 * w + bb]] = (uint8_t)(pre[q] >> (8 * bb));
+      }
+    }
+    __syncthreads();
+  }
   bool any = false;
-  for (int r = tid; r < ld; r += nthreads) {
-    const int v = acc[r] % P;
-    gn[r] = (uint8_t)v;
-    any |= v != 0;
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) {
+    const int r = tid + kThreads * o;
+    if (r < ld) {
+      const int v = acc[o] % P;
+      gn[r] = (uint8_t)v;
+      any |= v != 0;
+    }
   }
   return __syncthreads_or(any ? 1 : 0) != 0;
 }
@@ -1113,7 +1202,7 @@ __device__ __noinline__ int reduced_height(Smem &sm, uint8_t *gs, uint8_t *gn, u
     // q[r] = u(F Delta_1(f))[r] = sum_c Delta_1(f)[p r + (p-1,..,p-1) - c] F[c], r in B_4: one warp per r
     for (int r = warp; r < 35; r += nwarps) {
       int ur, sr, tr;
-      decode_packed(r, ur, sr, tr);
+      decode_packed(r, ur, sr, tr, 4);
       const int eu0 = P * ur + 3 * (P - 1), es0 = P * sr + 2 * (P - 1), et0 = P * tr + (P - 1);
       unsigned a = 0;
       // g column col = tri(uc) + sc of this lane, advanced 32 columns at a time
@@ -1136,17 +1225,18 @@ __device__ __noinline__ int reduced_height(Smem &sm, uint8_t *gs, uint8_t *gn, u
     bool any = false;
     for (int e = tid; e < Pr::ld; e += nthreads) {
       int ue, se, te;
-      decode_packed(e, ue, se, te);
+      decode_packed(e, ue, se, te, d);
       int acc = 0;
-      for (int I = 0; I < 35; ++I) {
-        const int qi = q[I];
-        if (!qi) continue;
-        int uI, sI, tI;
-        decode_packed(I, uI, sI, tI);
-        const int u2 = ue - uI, s2 = se - sI, t2 = te - tI;
-        if (t2 < 0 || s2 < t2 || u2 < s2 || u2 > dm) continue;
-        acc += qi * (int)fpm2[tet(u2) + tri(s2) + t2];
-      }
+      int I = 0;   // packed index tet(uI) + tri(sI) + tI of the tap
+      for (int uI = 0; uI <= 4; ++uI)
+        for (int sI = 0; sI <= uI; ++sI)
+          for (int tI = 0; tI <= sI; ++tI, ++I) {
+            const int qi = q[I];
+            if (!qi) continue;
+            const int u2 = ue - uI, s2 = se - sI, t2 = te - tI;
+            if (t2 < 0 || s2 < t2 || u2 < s2 || u2 > dm) continue;
+            acc += qi * (int)fpm2[tet(u2) + tri(s2) + t2];
+          }
       int v = -(acc % P);
       if (v < 0) v += P;
       Fn[e] = (uint8_t)v;
@@ -1191,17 +1281,21 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   }
   if (DEBUG)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
-  // A6 + A7.  p = 7: Delta streams through shared memory; other p: a guarded copy of Delta, built in the buffer
-  // that does not hold Delta, is gathered from directly
+  // A6 + A7.  Theta reads a copy of Delta built in the buffer that does not hold it: in residue-class order at
+  // p <= 7 (theta_poly), guarded at p >= 11 (theta_gather)
   uint32_t *dg = delta == bufA ? bufB : bufA;
-  if constexpr (!theta_streams<P>()) {
+  unsigned char *ringb = reinterpret_cast<unsigned char *>(ring);
+  if constexpr (theta_by_classes<P>()) {
+    poly_tables<P>(ringb);
+    delta_to_classes<P>(delta, dg, sm, ringb);
+  } else {
     delta_to_guarded<P>(delta, dg, sm);
-    __syncthreads();
   }
+  __syncthreads();
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
     bool nonzero;
-    if constexpr (theta_streams<P>()) nonzero = theta_stream<P>(delta, sm, g, g2, ring);
+    if constexpr (theta_by_classes<P>()) nonzero = theta_poly<P>(dg, g, g2, ringb);
     else nonzero = theta_gather<P>(dg, sm, g, g2, ring);
     theta_steps = h - 1;
     if (DEBUG)

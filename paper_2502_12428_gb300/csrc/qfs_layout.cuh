@@ -48,12 +48,38 @@ struct Prime {
   // witness monomial (x1 x2 x3 x4)^(p-1) in degree d: (u, s, t) = (3(p-1), 2(p-1), p-1)
   static constexpr int wu = 3 * (P - 1), ws = 2 * (P - 1), wt = P - 1;
   static constexpr int witness = tet(wu) + tri(ws) + wt;
+  // One chain output sums at most 35 products of a residue below p^2 and a coefficient below p.
+  static constexpr uint32_t chain_max = 35u * (p2 - 1) * (P - 1);
+  // a mod p^2 = a - p^2 floor(a M / 2^32) with M = ceil(2^32 / p^2): exact while a (M p^2 - 2^32) < 2^32, which
+  // holds far beyond chain_max for every p <= 13 (a host test checks every a <= chain_max).
+  static constexpr uint32_t mod_magic = (uint32_t)((0x100000000ull + p2 - 1) / p2);
+  static_assert((uint64_t)chain_max * ((uint64_t)mod_magic * p2 - 0x100000000ull) < 0x100000000ull,
+                "multiply-high reduction exact over the chain's range");
 };
+
+// a mod p^2 by one multiply-high (valid for a <= Prime<P>::chain_max).
+template <int P>
+__host__ __device__ __forceinline__ uint32_t mod_p2_mulhi(uint32_t a) {
+#if defined(__CUDA_ARCH__)
+  return a - (uint32_t)Prime<P>::p2 * __umulhi(a, Prime<P>::mod_magic);
+#else
+  return a - (uint32_t)Prime<P>::p2 * (uint32_t)(((uint64_t)a * Prime<P>::mod_magic) >> 32);
+#endif
+}
+
+// Index of the highest set bit of x > 0.
+__host__ __device__ inline int high_bit(unsigned x) {
+#if defined(__CUDA_ARCH__)
+  return 31 - __clz((int)x);
+#else
+  return 31 - __builtin_clz(x);
+#endif
+}
 
 // floor(sqrt(x)) for 0 <= x < 2^30, digit by digit (integer arithmetic only).
 __host__ __device__ inline int isqrt(int x) {
-  int r = 0, bit = 1 << 28;
-  while (bit > x) bit >>= 2;
+  if (x <= 0) return 0;
+  int r = 0, bit = 1 << (high_bit((unsigned)x) & ~1);   // the highest power of four <= x
   while (bit != 0) {
     if (x >= r + bit) {
       x -= r + bit;
@@ -66,9 +92,9 @@ __host__ __device__ inline int isqrt(int x) {
   return r;
 }
 
-// floor(cbrt(x)) for 0 <= x < 2^30, by bisection.
-__host__ __device__ inline int icbrt(int x) {
-  int lo = 0, hi = 1024;   // lo^3 <= x < hi^3
+// floor(cbrt(x)) for 0 <= x < min(2^30, hi^3), by bisection.
+__host__ __device__ inline int icbrt(int x, int hi = 1024) {
+  int lo = 0;   // lo^3 <= x < hi^3
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if ((int64_t)mid * mid * mid <= x) lo = mid; else hi = mid;
@@ -122,8 +148,9 @@ __device__ __forceinline__ void decode_form_chunk(int k, int m, const int *SW, i
 }
 
 // Packed index i of a form (degree <= kMaxD) -> (u, s, t).
-__host__ __device__ inline void decode_packed(int i, int &u, int &s, int &t) {
-  int uu = icbrt(6 * i);
+__host__ __device__ inline void decode_packed(int i, int &u, int &s, int &t, int max_deg = kMaxD) {
+  // the slice u satisfies u^3 <= 6 tet(u) <= 6 i, and u <= max_deg for an index of a form of degree max_deg
+  int uu = icbrt(6 * i, max_deg + 2);
   while (uu > 0 && tet(uu) > i) --uu;
   while (tet(uu + 1) <= i) ++uu;
   int rem = i - tet(uu);

@@ -240,7 +240,7 @@ __device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem 
     uint32_t w[2] = {0u, 0u}, gw[2] = {0u, 0u};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      int G = (int)((uint32_t)acc[J][j] % (uint32_t)Pr::p2);  // acc >= 0; outputs past the column's end are zero
+      int G = (int)mod_p2_mulhi<P>((uint32_t)acc[J][j]);  // acc >= 0; outputs past the column's end are zero
       if (LAST) {
         const int t = 8 * L.h + j;
         if (DEBUG) gw[j >> 2] |= (uint32_t)G << (8 * (j & 3));
@@ -251,7 +251,9 @@ __device__ __forceinline__ void finalize(uint32_t *__restrict__ out, const Smem 
         if (G % P) bad = true;
         G /= P;
       }
-      w[j >> 2] |= (uint32_t)G << (8 * (j & 3));
+      // byte j & 3 of word j >> 2; a multiply-add (the bytes do not overlap), which keeps the packing off the
+      // byte-permute pipe that the windows load
+      w[j >> 2] += (uint32_t)G * (1u << (8 * (j & 3)));
     }
     const int o = sm.SW[u] + L.out_off;
     if (L.pad == 1) {

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) theta_matrix_fill(const uint32_t *ws
   build_sw(SW, D + 2);
   for (int c = threadIdx.x; c < ld; c += blockDim.x) {
     int u, s, t;
-    decode_packed(c, u, s, t);
+    decode_packed(c, u, s, t, d);
     cst[c] = (uint32_t)u | ((uint32_t)s << 10) | ((uint32_t)t << 20);
   }
   __syncthreads();
@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(kThreads) theta_matrix_fill(const uint32_t *ws
       Mq[(size_t)r * ld + c] = v;
     }
   }
-  (void)d;
 }
 
 template <int P>

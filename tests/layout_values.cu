@@ -55,13 +55,36 @@ void decoder_lines() {
         decode_packed(i, u2, s2, t2);
         if (u2 != u || s2 != s || t2 != t) ++bad_packed;
       }
+  // the bounded form the kernels use for forms of degree 4 (reduced theta) and d = 4(p-1)
+  const int degs[6] = {4, 8, 16, 24, 40, 48};
+  for (int k = 0; k < 6; ++k) {
+    int j = 0;
+    for (int u = 0; u <= degs[k]; ++u)
+      for (int s = 0; s <= u; ++s)
+        for (int t = 0; t <= s; ++t, ++j) {
+          int u2, s2, t2;
+          decode_packed(j, u2, s2, t2, degs[k]);
+          if (u2 != u || s2 != s || t2 != t) ++bad_packed;
+        }
+  }
   std::printf("\"decoder_mismatches\": {\"isqrt\": %ld, \"icbrt\": %ld, \"half\": %ld, \"chunk\": %ld, "
               "\"packed\": %ld, \"packed_entries\": %d},\n", bad_sqrt, bad_cbrt, bad_half, bad_chunk, bad_packed, i);
+}
+
+// Values a <= chain_max where the multiply-high reduction differs from a % p^2 (zero when it is exact).
+template <int P>
+long mod_mismatches() {
+  long bad = 0;
+  for (uint32_t a = 0; a <= Prime<P>::chain_max; ++a)
+    if (mod_p2_mulhi<P>(a) != a % (uint32_t)Prime<P>::p2) ++bad;
+  return bad;
 }
 
 int main() {
   std::printf("{\"max_d\": %d,\n", kMaxD);
   decoder_lines();
+  std::printf("\"mod_mismatches\": [%ld, %ld, %ld, %ld, %ld],\n", mod_mismatches<3>(), mod_mismatches<5>(),
+              mod_mismatches<7>(), mod_mismatches<11>(), mod_mismatches<13>());
   std::printf("\"chunks_of\": [");
   for (int s = 0; s <= kMaxD + 2; ++s) std::printf("%s%d", s ? "," : "", chunks_of(s));
   std::printf("],\n\"chunk_prefix\": [");

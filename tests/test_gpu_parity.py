@@ -69,17 +69,49 @@ def test_stages_p5(qfs, form):
         check_stages(qfs, 5, row, form)
 
 
+def _route_a_parallel(p, rows):
+    # route A releases the interpreter while it runs (ctypes), so one thread per quartic runs them side by side
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=len(rows)) as ex:
+        return list(ex.map(lambda r: oracle.stage_arrays_a(p, r), rows))
+
+
 @pytest.mark.slow
 def test_stages_p7(qfs):
-    row = next(r[3] for r in example_quartics() if r[0] == 7 and r[1] == 2)  # one quartic, every form
-    ref = oracle.stage_arrays_a(7, row)
+    # Figure 5's rows of height 2, 3 and infinity and a sparse quartic of height >= 3, every form, every array
+    ex = {r[1]: r[3] for r in example_quartics() if r[0] == 7}
+    fs, hs = find_rows(7, 3000, 7070, lambda x: x >= 3, 1, gen=inputs.sparse)
+    rows = [ex[2], ex[3], ex[0], fs[0]]
+    refs = _route_a_parallel(7, rows)
+    assert [r["h"] for r in refs[:3]] == [2, 3, 0] and refs[3]["h"] >= 3
+    for row, ref in zip(rows, refs):
+        for form in CORE_FORMS:
+            got = qfs.debug_stages(7, dev_tensor(row), form=form)
+            assert got["h"] == ref["h"]
+            assert np.array_equal(got["g"].cpu().numpy(), ref["g"])
+            assert np.array_equal(got["G"].cpu().numpy(), ref["D"])
+            assert np.array_equal(got["delta"].cpu().numpy(), ref["delta"])
+            n_it = ref["iters"].shape[0]
+            assert n_it >= 1
+            assert np.array_equal(got["iters"].cpu().numpy()[:n_it], ref["iters"])
+
+
+@pytest.mark.slow
+def test_stages_p11(qfs):
+    # Figure 6's row of height 2 at p = 11 (per-CTA buffers above 15 MB): g, G and Delta against the oracle's stage
+    # arrays with D formed by products with f (equal to route A's lift(g)^p, pinned on CPU), the iterate against
+    # route R (equal to route A's iterates, pinned on CPU)
+    row = next(r[3] for r in example_quartics() if r[0] == 11 and r[1] == 2)
+    ref = oracle.stage_arrays_fchain(11, row)
+    it = oracle.stage_arrays_r(11, row)
+    assert not ref["h1"] and it["h"] == 2
     for form in CORE_FORMS:
-        got = qfs.debug_stages(7, dev_tensor(row), form=form)
-        assert got["h"] == ref["h"] == 2
+        got = qfs.debug_stages(11, dev_tensor(row), form=form)
+        assert got["h"] == 2
         assert np.array_equal(got["g"].cpu().numpy(), ref["g"])
         assert np.array_equal(got["G"].cpu().numpy(), ref["D"])
         assert np.array_equal(got["delta"].cpu().numpy(), ref["delta"])
-        assert np.array_equal(got["iters"].cpu().numpy()[:1], ref["iters"])
+        assert np.array_equal(got["iters"].cpu().numpy()[:1], it["iters"])
 
 
 # ------------------------------------------------------------------------------------- heights, small sets

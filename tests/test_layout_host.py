@@ -93,3 +93,9 @@ def test_integer_index_decoders(values):
     assert m["packed_entries"] == math.comb(values["max_d"] + 3, 3)
     assert {k: v for k, v in m.items() if k != "packed_entries"} == {"isqrt": 0, "icbrt": 0, "half": 0, "chunk": 0,
                                                                       "packed": 0}
+
+
+def test_chain_reduction_by_multiply_high(values):
+    # the chain's outputs reduce mod p^2 by one multiply-high; it equals a % p^2 for every value a chain output
+    # can take (35 products of a residue below p^2 and a coefficient below p)
+    assert values["mod_mismatches"] == [0, 0, 0, 0, 0]

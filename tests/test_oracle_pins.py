@@ -237,6 +237,30 @@ def test_route_a_equals_route_r(p, n):
     assert checked_iters > 0
 
 
+@pytest.mark.parametrize("p,n", [(3, 60), (5, 40)])
+def test_fchain_stage_arrays_equal_route_a(p, n):
+    # D formed as lift(f)^(p(p-1)) by products with f's 35 terms equals route A's lift(g)^p (Sec. 3 reading on the
+    # lift: (c + p b)^p = c^p mod p^2), and Algorithm 1's subtraction and division then give route A's Delta
+    f = np.concatenate([inputs.dense(p, n, 5100 + p), inputs.sparse(p, n // 2, 5200 + p)])
+    checked = 0
+    for row in f:
+        a = oracle.stage_arrays_a(p, row)
+        c = oracle.stage_arrays_fchain(p, row)
+        assert np.array_equal(a["g"], c["g"])
+        assert c["h1"] == (a["h"] == 1)
+        if a["h"] != 1:
+            assert np.array_equal(a["D"], c["D"]) and np.array_equal(a["delta"], c["delta"])
+            checked += 1
+    assert checked > 5
+
+
+def test_fchain_stage_arrays_equal_route_a_p7():
+    row = next(r[3] for r in example_quartics() if r[0] == 7 and r[1] == 2)
+    a = oracle.stage_arrays_a(7, row)
+    c = oracle.stage_arrays_fchain(7, row)
+    assert np.array_equal(a["D"], c["D"]) and np.array_equal(a["delta"], c["delta"])
+
+
 # ---------------------------------------------------------------- invariance and statistics
 @pytest.mark.parametrize("p,n", [(5, 300), (7, 150)])
 def test_pgl4_invariance_route_r(p, n):
