@@ -524,7 +524,8 @@ __host__ __device__ constexpr bool theta_by_classes() { return P <= 7; }
 template <int P>
 struct Poly {
   static constexpr int d = 4 * (P - 1), ld = tet(d + 1);
-  static constexpr int C = d + 4;                       // cube side: coordinates -3 .. d
+  static constexpr int pad = 4;                         // zero layers before coordinate 0 (kernels of degree <= 4)
+  static constexpr int C = d + 1 + pad;                 // cube side: coordinates -pad .. d
   static constexpr int CB = (C * C * C + 15) & ~15;     // bytes of one cube
   static constexpr int NCLS = P * P * P;
   static constexpr int NOUT = (ld + kThreads - 1) / kThreads;   // outputs per thread
@@ -535,7 +536,11 @@ struct Poly {
   static constexpr int cubeaddr_off = tapsrc_off + ((2 * ld + 15) & ~15);
   static constexpr int cls_off = cubeaddr_off + ((2 * ld + 15) & ~15);
   static constexpr int cnt_off = cls_off + 16 * NCLS;
-  static constexpr int bytes = cnt_off + 16;
+  // identity power mode: the taps of Delta_1(f) split by class (C(4p+3, 3) bytes in all)
+  static constexpr int idtaps_off = cnt_off + 16;
+  // byte offset of each class in the class-ordered copy, indexed by sigma2 + p sigma3 + p^2 sigma4 (NCLS ints)
+  static constexpr int sig_off = idtaps_off + ((tet(4 * P + 1) + 15) & ~15);
+  static constexpr int bytes = sig_off + 4 * NCLS;
 };
 
 // Classes of degree k (kernel degree) in residue-class order: rho in [0,p)^4 with |rho| = d - p k.
@@ -675,7 +680,8 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
 
 // Class records of theta_poly (ring, Poly<P>::cls_off): x = byte offset of Delta_sigma in the class-ordered copy,
 // y = offset of g_rho's taps in the tap arrays, z = k | Su << 8 | Ss << 16 | St << 24 where (Su, Ss, St) is sigma in
-// (u, s, t) coordinates (Delta_sigma[u', s', t'] = Delta[p u' + Su, p s' + Ss, p t' + St]).  Classes are ordered by
+// (u, s, t) coordinates (Delta_sigma[u', s', t'] = Delta[p u' + Su, p s' + Ss, p t' + St]), w = offset of the class's
+// taps of Delta_1(f) (degree 4 - k; the identity power mode).  Classes are ordered by
 // k, which theta_poly's cube clearing relies on; inside one k the order is whatever the atomic counters hand out.
 // Also fills the tap sources (the packed index in B_d of g_rho's tap c', in the packed order of c' in B_k) and the
 // cube address of every packed index of B_d.  Ends with a barrier.
@@ -692,7 +698,7 @@ __device__ __forceinline__ void poly_tables(unsigned char *ring) {
   for (int i = tid; i < Q::ld; i += nthreads) {
     int u, s, t;
     decode_packed(i, u, s, t, d);
-    cubeaddr[i] = (uint16_t)((u + 3) * C * C + (s + 3) * C + t + 3);
+    cubeaddr[i] = (uint16_t)((u + Q::pad) * C * C + (s + Q::pad) * C + t + Q::pad);
   }
   __syncthreads();
   constexpr int NQ = (Q::NCLS + kThreads - 1) / kThreads;
@@ -716,16 +722,19 @@ __device__ __forceinline__ void poly_tables(unsigned char *ring) {
     const int r2 = x % P, r3 = (x / P) % P, r4 = x / (P * P);
     const int r1 = ((d - r2 - r3 - r4) % P + P) % P;
     const int k = (d - (r1 + r2 + r3 + r4)) / P;
-    int j = slot[q], goff = 0, toff = 0;
+    int j = slot[q], goff = 0, toff = 0, ioff = 0;
     for (int kk = 0; kk < k; ++kk) {
       j += cnt[kk];
       goff += cnt[kk] * poly_class_bytes(P, kk);
       toff += cnt[kk] * tet(kk + 1);
+      ioff += cnt[kk] * tet(4 - kk + 1);
     }
     goff += slot[q] * poly_class_bytes(P, k);
     toff += slot[q] * tet(k + 1);
+    ioff += slot[q] * tet(4 - k + 1);
     const int s2 = P - 1 - r2, s3 = P - 1 - r3, s4 = P - 1 - r4;
-    cls[j] = make_int4(goff, toff, k | ((s2 + s3 + s4) << 8) | ((s3 + s4) << 16) | (s4 << 24), 0);
+    cls[j] = make_int4(goff, toff, k | ((s2 + s3 + s4) << 8) | ((s3 + s4) << 16) | (s4 << 24), ioff);
+    reinterpret_cast<int *>(ring + Q::sig_off)[s2 + P * s3 + P * P * s4] = goff;
     // taps: g[p c' + rho] for c' = (uc, sc, tc) in B_k, rho = (r2 + r3 + r4, r3 + r4, r4) in (u, s, t)
     int i = 0;
     for (int uc = 0; uc <= k; ++uc)
@@ -736,36 +745,35 @@ __device__ __forceinline__ void poly_tables(unsigned char *ring) {
   __syncthreads();
 }
 
-// Padded Delta (degree D) -> class order: class j holds Delta_sigma in packed order of B_{d-k} at byte offset
-// cls[j].x of `dc`.  One thread per destination word (four consecutive packed indices of one class); the bytes are
-// read from the padded layout at (p u' + Su, p s' + Ss, p t' + St).  Classes of the same (sigma2, sigma3 + sigma4)
-// read the same Delta columns.  The caller synchronises the CTA afterwards.
+// Padded Delta (degree D) -> class order: class sigma holds Delta_sigma in packed order of B_{d-k}, starting at byte
+// sig_off[sigma] of `dc`.  One thread per 16-byte chunk of the padded Delta, read once and coalesced; each byte
+// (U, S, T) goes to class sigma = (e2, e3, e4) mod p at the packed index of (e - sigma) / p, where
+// (e2, e3, e4) = (U - S, S - T, T).  Within a chunk T advances by one, so e4 / p, e4 mod p, e3 / p and e3 mod p
+// advance incrementally.  The caller synchronises the CTA afterwards.
 template <int P>
 __device__ __forceinline__ void delta_to_classes(const uint32_t *__restrict__ delta, uint32_t *__restrict__ dc,
                                                  const Smem &sm, const unsigned char *ring) {
-  using Q = Poly<P>;
-  constexpr int C = Q::C;
-  const uint16_t *cubeaddr = reinterpret_cast<const uint16_t *>(ring + Q::cubeaddr_off);
-  const int4 *cls = reinterpret_cast<const int4 *>(ring + Q::cls_off);
-  const uint8_t *db = reinterpret_cast<const uint8_t *>(delta);
-  for (int j = 0; j < Q::NCLS; ++j) {
-    const int4 c = cls[j];
-    const int k = c.z & 255, Su = (c.z >> 8) & 255, Ss = (c.z >> 16) & 255, St = (c.z >> 24) & 255;
-    const int len = tet(Q::d - k + 1);
-    for (int w = threadIdx.x; 4 * w < len; w += blockDim.x) {
-      uint32_t word = 0;
+  constexpr int D = Prime<P>::D;
+  const int *sig = reinterpret_cast<const int *>(ring + Poly<P>::sig_off);
+  uint8_t *db = reinterpret_cast<uint8_t *>(dc);
+  const int nchunks = sm.SW[D + 1] / 4;
+  for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
+    int U, S, c;
+    decode_form_chunk(k, D, sm.SW, U, S, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(delta + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const int e2 = U - S, q2 = e2 / P, r2 = e2 - P * q2;
+    const int T0 = 16 * c;
+    int q4 = T0 / P, r4 = T0 - P * q4;                 // e4 = T
+    int q3 = (S - T0) / P, r3 = (S - T0) - P * q3;     // e3 = S - T (>= 0 while T <= S)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = 4 * w + b;
-        if (i < len) {
-          // (u', s', t') of packed index i from its cube address
-          const int a = cubeaddr[i];
-          const int u = a / (C * C) - 3, s = (a / C) % C - 3, t = a % C - 3;
-          const int U = P * u + Su, S = P * s + Ss, T = P * t + St;
-          word |= (uint32_t)db[4 * (sm.SW[U] + colw(S)) + T] << (8 * b);
-        }
+    for (int b = 0; b < 16; ++b) {
+      if (T0 + b <= S) {
+        const int up = q2 + q3 + q4, sp = q3 + q4;
+        db[sig[r2 + P * r3 + P * P * r4] + tet(up) + tri(sp) + q4] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
       }
-      dc[c.x / 4 + w] = word;
+      if (++r4 == P) { r4 = 0; ++q4; }
+      if (--r3 < 0) { r3 = P - 1; --q3; }
     }
   }
 }
@@ -813,12 +821,12 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
   for (int i = tid; i < ld; i += nthreads) taps[i] = g[tapsrc[i]];
   for (int i = tid; i < 2 * Q::CB / 16; i += nthreads) reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  // output addresses: r_o = tid + kThreads o; threads past B_d read the (zero) cube at output (0, 0, 0)
+  // output addresses: r_o = tid + kThreads o; threads past B_d read the cube around output (0, 0, 0), and drop it
   int a[NOUT], acc[NOUT];
 #pragma unroll
   for (int o = 0; o < NOUT; ++o) {
     const int r = tid + kThreads * o;
-    a[o] = r < ld ? (int)cubeaddr[r] : 3 * C * C + 3 * C + 3;
+    a[o] = r < ld ? (int)cubeaddr[r] : Q::pad * (C * C + C + 1);
     acc[o] = 0;
   }
   // class 0 into cube 0
@@ -991,6 +999,94 @@ __device__ __forceinline__ void power_to_G(Smem &sm, const uint8_t *gs, uint32_t
   __syncthreads();
 }
 
+// The identity power mode at p <= 7, by residue classes: Delta_1(f^(p-1)) = E(x^p) - f^(p-2)(x^p) Delta_1(f) (mod p)
+// (see power_identity) is formed directly in theta_poly's class order.  Splitting Delta_1(f) = sum_sigma
+// x^sigma D_sigma(x^p) by the residues sigma of its exponents gives, class by class,
+//     Delta_sigma = [sigma = 0] E - f^(p-2) * D_sigma,   D_sigma[c'] = Delta_1(f)[p c' + sigma],  deg D_sigma = 4 - k,
+// so every class is a product of the same f^(p-2) (one zero-padded cube in shared memory, loaded once) with a kernel of
+// at most 35 taps: about 8e6 MACs per quartic at p = 7 for the whole Delta, and no barrier between classes.  Inputs:
+// f^(p-2), Delta_1(f) and E packed (mod p) in global memory; output: the class-ordered copy `dc` that theta_poly
+// reads.  poly_tables must have run.  In debug mode the padded Delta is also written to dbg.delta.
+template <int P, bool DEBUG>
+__device__ __noinline__ void identity_classes(const uint8_t *__restrict__ fpm2_g, const uint8_t *__restrict__ d1f_g,
+                                              const uint8_t *__restrict__ E_g, uint32_t *__restrict__ dc,
+                                              const Smem &sm, unsigned char *ring, DebugPtrs dbg) {
+  using Q = Poly<P>;
+  constexpr int d = Q::d, C = Q::C, NOUT = Q::NOUT, l_fpm2 = tet(4 * (P - 2) + 1), l_d1f = tet(4 * P + 1);
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  uint8_t *cube = ring;                       // f^(p-2), zero outside its cone
+  uint8_t *d1f = ring + Q::CB;                // Delta_1(f) and E, packed, in the second cube's space
+  uint8_t *E = d1f + l_d1f;
+  uint8_t *dt = ring + Q::idtaps_off;
+  const uint16_t *cubeaddr = reinterpret_cast<const uint16_t *>(ring + Q::cubeaddr_off);
+  const int4 *cls = reinterpret_cast<const int4 *>(ring + Q::cls_off);
+  for (int i = tid; i < Q::CB / 16; i += nthreads) reinterpret_cast<uint4 *>(cube)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < l_d1f; i += nthreads) d1f[i] = d1f_g[i];
+  for (int i = tid; i < Q::ld; i += nthreads) E[i] = E_g[i];
+  __syncthreads();
+  for (int i = tid; i < l_fpm2; i += nthreads) cube[cubeaddr[i]] = fpm2_g[i];
+  // taps of every class: D_sigma[c'] = Delta_1(f)[(p u_c + Su, p s_c + Ss, p t_c + St)], c' in B_{4-k}
+  for (int j = tid; j < Q::NCLS; j += nthreads) {
+    const int4 c = cls[j];
+    const int k = c.z & 255, Su = (c.z >> 8) & 255, Ss = (c.z >> 16) & 255, St = (c.z >> 24) & 255;
+    int i = 0;
+    for (int uc = 0; uc <= 4 - k; ++uc)
+      for (int sc = 0; sc <= uc; ++sc)
+        for (int tc = 0; tc <= sc; ++tc, ++i)
+          dt[c.w + i] = d1f[tet(P * uc + Su) + tri(P * sc + Ss) + P * tc + St];
+  }
+  __syncthreads();
+  int a[NOUT];
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) {
+    const int r = tid + kThreads * o;
+    a[o] = r < Q::ld ? (int)cubeaddr[r] : Q::pad * (C * C + C + 1);
+  }
+  uint8_t *dcb = reinterpret_cast<uint8_t *>(dc);
+  for (int j = 0; j < Q::NCLS; ++j) {
+    const int4 c = cls[j];
+    const int k = c.z & 255;
+    int acc[NOUT];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) acc[o] = 0;
+    const uint8_t *tp = dt + c.w;
+    switch (k) {
+      case 0: poly_macs<P, 4>(cube, tp, a, acc); break;
+      case 1: poly_macs<P, 3>(cube, tp, a, acc); break;
+      case 2: poly_macs<P, 2>(cube, tp, a, acc); break;
+      default: poly_macs<P, 1>(cube, tp, a, acc); break;
+    }
+    const int len = tet(d - k + 1);
+    const bool lattice = ((c.z >> 8) & 0xFFFFFF) == 0;   // sigma = 0: the class that receives E(x^p)
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+      const int r = tid + kThreads * o;
+      if (r < len) {
+        int v = -(acc[o] % P);
+        if (lattice) v += E[r];
+        if (v < 0) v += P;
+        dcb[c.x + r] = (uint8_t)v;
+      }
+    }
+  }
+  if (DEBUG) {
+    // the padded Delta for the parity hook: every word cleared, then each class's bytes at (p u' + Su, ...)
+    __syncthreads();
+    for (int k2 = tid; k2 < sm.SW[Prime<P>::D + 1]; k2 += nthreads) dbg.delta[k2] = 0u;
+    __syncthreads();
+    uint8_t *pd = reinterpret_cast<uint8_t *>(dbg.delta);
+    for (int j = 0; j < Q::NCLS; ++j) {
+      const int4 c = cls[j];
+      const int k = c.z & 255, Su = (c.z >> 8) & 255, Ss = (c.z >> 16) & 255, St = (c.z >> 24) & 255;
+      for (int r = tid; r < tet(d - k + 1); r += nthreads) {
+        const int ca = cubeaddr[r];
+        const int u = ca / (C * C) - Q::pad, s = (ca / C) % C - Q::pad, t = ca % C - Q::pad;
+        pd[4 * (sm.SW[P * u + Su] + colw(P * s + Ss)) + P * t + St] = dcb[c.x + r];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ identity power
 // A4 + A5 by an exact algebraic shortcut (power mode QFS_POWER_IDENTITY).  It produces the same Delta_1(f^(p-1))
 // array as the chain, and the chain stays the literal reading of Algorithm 1.
@@ -1092,6 +1188,15 @@ __device__ __noinline__ uint32_t *power_identity(Smem &sm, const uint8_t *gs, ui
     }
   }
   __syncthreads();
+  if constexpr (theta_by_classes<P>()) {
+    // Delta straight into theta's class order, in `cur` (the products above are done with it)
+    if (bad) atomicOr(status, kStatusInexactDivision);
+    unsigned char *ringb = reinterpret_cast<unsigned char *>(ring);
+    poly_tables<P>(ringb);
+    identity_classes<P, DEBUG>(fpm2_g, d1f_g, E_g, cur, sm, ringb, dbg);
+    __syncthreads();
+    return cur;
+  }
   // stage the three small arrays in shared memory
   uint8_t *fpm2 = reinterpret_cast<uint8_t *>(ring), *d1f = fpm2 + l_fpm2, *E = d1f + l_d1f;
   for (int i = tid; i < l_fpm2 + l_d1f + l_E; i += nthreads) fpm2[i] = fpm2_g[i];
@@ -1273,21 +1378,27 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   // A4 + A5 into `other` or `cur`, whichever the chain's parity leaves last
   constexpr int nsteps = P * (P - 1) - (P - 1);   // products from f~^(p-1) to f~^(p(p-1))
   uint32_t *delta;
+  // the identity mode at p <= 7 leaves Delta already in theta's class order (and the debug copy written)
+  const bool in_classes = power_mode == 1 && theta_by_classes<P>();
   if (power_mode == 1) {
     delta = power_identity<P, FORM, DEBUG>(sm, gs, ring, cur, other, status, dbg);
   } else {
     delta = (nsteps % 2) ? other : cur;
     power_to_G<P, FORM, true, DEBUG>(sm, gs, ring, cur, other, nullptr, status, dbg);
   }
-  if (DEBUG)
+  if (DEBUG && !in_classes)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
   // A6 + A7.  Theta reads a copy of Delta built in the buffer that does not hold it: in residue-class order at
   // p <= 7 (theta_poly), guarded at p >= 11 (theta_gather)
   uint32_t *dg = delta == bufA ? bufB : bufA;
   unsigned char *ringb = reinterpret_cast<unsigned char *>(ring);
   if constexpr (theta_by_classes<P>()) {
-    poly_tables<P>(ringb);
-    delta_to_classes<P>(delta, dg, sm, ringb);
+    if (in_classes) {
+      dg = delta;
+    } else {
+      poly_tables<P>(ringb);
+      delta_to_classes<P>(delta, dg, sm, ringb);
+    }
   } else {
     delta_to_guarded<P>(delta, dg, sm);
   }

@@ -8,11 +8,15 @@
 //   2. For each of P word-size primes q = c 2^24 + 1: reduce the coefficients mod q, forward transform
 //      (Gentleman-Sande, natural order in, bit-reversed order out), raise every entry to the n-th power, inverse
 //      transform (Cooley-Tukey, bit-reversed in, natural out), and gather the coefficients of the degree-d n output
-//      monomials (times N^-1).
+//      monomials (times N^-1).  The transforms run in passes of up to 8 radix-2 stages in shared memory (the
+//      four-step split of a length-M transform into R-point transforms over columns of stride M / R, twiddles
+//      w_M^(c k) between passes); the last forward pass, the n-th powers and the first inverse pass share one
+//      kernel, so a length-2^24 transform pair costs five round trips through device memory instead of 48.
 //   3. Chinese remaindering (Garner's mixed-radix form) of the P residues of every coefficient into a 256-bit
 //      unsigned integer.  P is the smallest number of primes whose product exceeds the coefficient bound
 //      (sum of |coefficients|)^n, so the result is exact.
-// Modular products use Barrett reduction with mu = floor(2^64 / q).
+// Modular products use Barrett reduction with mu = floor(2^64 / q), and Shoup's method (a precomputed
+// floor(w 2^32 / q) for each fixed multiplier w) for the twiddle factors.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -50,14 +54,6 @@ struct PrimeQ {
   uint64_t mu;
 };
 
-// tw[k] = w^k, itw[k] = w^-k for k < N/2, with w a primitive N-th root of unity mod q
-__global__ void twiddle_kernel(uint32_t *tw, uint32_t *itw, uint32_t half, uint32_t w, uint32_t wi, PrimeQ P) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < half; k += gridDim.x * blockDim.x) {
-    tw[k] = powmod(w, k, P.q, P.mu);
-    itw[k] = powmod(wi, k, P.q, P.mu);
-  }
-}
-
 // a = 0, then the packed input reduced mod q
 __global__ void zero_kernel(uint32_t *a, uint32_t N) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) a[i] = 0;
@@ -73,28 +69,156 @@ __global__ void scatter_kernel(const uint32_t *coeffs, int d, int B, uint32_t *a
   }
 }
 
-// one Gentleman-Sande stage (block length len, twiddle stride N / len): a[i0], a[i1] -> a[i0] + a[i1], (a[i0] - a[i1]) w^j
-__global__ void dif_stage(uint32_t *a, uint32_t N, uint32_t half, uint32_t tstride, const uint32_t *tw, PrimeQ P) {
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < N / 2; t += gridDim.x * blockDim.x) {
-    const uint32_t j = t & (half - 1), i0 = ((t - j) << 1) + j, i1 = i0 + half;
-    const uint32_t u = a[i0], v = a[i1];
-    a[i0] = addmod(u, v, P.q);
-    a[i1] = mulmod(submod(u, v, P.q), tw[j * tstride], P.q, P.mu);
+// a w mod q for a < 2^32, w < q < 2^31, given ws = floor(w 2^32 / q) (Shoup): the quotient estimate
+// floor(a ws / 2^32) is at most one below floor(a w / q), so a w - est q lies in [0, 2q)
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t a, uint32_t w, uint32_t ws, uint32_t q) {
+  const uint32_t est = __umulhi(a, ws);
+  const uint32_t r = a * w - est * q;
+  return r >= q ? r - q : r;
+}
+
+// Twiddle tables of one prime and direction: lo[j] = w^j (j < 4096), hi[j] = w^(4096 j) (j < max(1, N / 4096)),
+// each with its Shoup companion, so that w^e = lo[e mod 4096] hi[e / 4096]; rt[j] = w_R^j (j < R / 2) for the
+// R-point transforms inside a pass, R = min(256, N), also with companions.
+struct TwTab {
+  const uint32_t *lo, *los, *hi, *his, *rt, *rts;
+};
+constexpr int kTwLoBits = 12;
+constexpr int kPassMaxStages = 8;
+constexpr int kPassR = 1 << kPassMaxStages;   // longest column of a pass
+constexpr int kPassCols = 32;                 // columns per block in the column passes
+constexpr int kTileWords = kPassR * (kPassCols + 1);
+
+__device__ __forceinline__ uint32_t twiddle_apply(uint32_t x, uint32_t e, const TwTab &T, uint32_t q) {
+  const uint32_t lo = e & ((1u << kTwLoBits) - 1), hi = e >> kTwLoBits;
+  x = shoup_mul(x, __ldg(T.lo + lo), __ldg(T.los + lo), q);
+  return shoup_mul(x, __ldg(T.hi + hi), __ldg(T.his + hi), q);
+}
+
+// table[j] = base^(j * step), comp[j] = floor(table[j] 2^32 / q), for j < n
+__global__ void power_table_kernel(uint32_t *table, uint32_t *comp, uint32_t n, uint32_t base, uint32_t step,
+                                   PrimeQ P) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t v = powmod(powmod(base, step, P.q, P.mu), j, P.q, P.mu);
+    table[j] = v;
+    comp[j] = (uint32_t)(((uint64_t)v << 32) / P.q);
   }
 }
-// one Cooley-Tukey stage: a[i0], a[i1] -> a[i0] + a[i1] w^j, a[i0] - a[i1] w^j
-__global__ void dit_stage(uint32_t *a, uint32_t N, uint32_t half, uint32_t tstride, const uint32_t *tw, PrimeQ P) {
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < N / 2; t += gridDim.x * blockDim.x) {
-    const uint32_t j = t & (half - 1), i0 = ((t - j) << 1) + j, i1 = i0 + half;
-    const uint32_t u = a[i0], v = mulmod(a[i1], tw[j * tstride], P.q, P.mu);
-    a[i0] = addmod(u, v, P.q);
-    a[i1] = submod(u, v, P.q);
+
+__device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
+
+// R-point DIF (natural in, bit-reversed out) on the columns of a shared tile: element m of column cc at
+// tile[m * ld + cc], ncol columns; twiddles w_R^j from rt (stage of length len uses w_R^(j R / len)).
+__device__ __forceinline__ void tile_dif(uint32_t *tile, int ld, int ncol, int R, const uint32_t *rt,
+                                         const uint32_t *rts, uint32_t q) {
+  for (int len = R; len >= 2; len >>= 1) {
+    const int h = len >> 1, ts = R / len;
+    for (int t = threadIdx.x; t < ncol * (R >> 1); t += blockDim.x) {
+      const int cc = t % ncol, b = t / ncol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+      const uint32_t u = tile[i0 * ld + cc], v = tile[i1 * ld + cc];
+      tile[i0 * ld + cc] = addmod(u, v, q);
+      tile[i1 * ld + cc] = shoup_mul(submod(u, v, q), rt[j * ts], rts[j * ts], q);
+    }
+    __syncthreads();
   }
 }
-__global__ void pow_kernel(uint32_t *a, uint32_t N, uint32_t n, PrimeQ P) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-    a[i] = powmod(a[i], n, P.q, P.mu);
+// R-point inverse DIT (bit-reversed in, natural out), twiddles w_R^-j
+__device__ __forceinline__ void tile_dit(uint32_t *tile, int ld, int ncol, int R, const uint32_t *rt,
+                                         const uint32_t *rts, uint32_t q) {
+  for (int len = 2; len <= R; len <<= 1) {
+    const int h = len >> 1, ts = R / len;
+    for (int t = threadIdx.x; t < ncol * (R >> 1); t += blockDim.x) {
+      const int cc = t % ncol, b = t / ncol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+      const uint32_t u = tile[i0 * ld + cc], v = shoup_mul(tile[i1 * ld + cc], rt[j * ts], rts[j * ts], q);
+      tile[i0 * ld + cc] = addmod(u, v, q);
+      tile[i1 * ld + cc] = submod(u, v, q);
+    }
+    __syncthreads();
+  }
 }
+
+// The R-point roots of a pass, from the table of Rmax-point roots (Rmax = min(kPassR, N)): w_R^j = w_Rmax^(j Rmax / R).
+__device__ __forceinline__ void load_root_table(uint32_t *rt, uint32_t *rts, const TwTab &T, int R, int logN) {
+  const int rmax = 1 << (logN < kPassMaxStages ? logN : kPassMaxStages);
+  for (int j = threadIdx.x; j < (R >> 1); j += blockDim.x) {
+    rt[j] = T.rt[j * (rmax / R)];
+    rts[j] = T.rts[j * (rmax / R)];
+  }
+}
+
+// A column pass of the length-N transform on blocks of M = R Nc elements (Nc >= kPassCols): column q = (block bb,
+// offset c) holds a[bb M + c + m Nc], m < R.  Forward (INV = false): R-point DIF of every column, then element m of
+// column c times w_M^(c k), k = bitrev(m) (its frequency index).  Inverse: the twiddle w_M^(-c k) first, then the
+// R-point inverse DIT.  Each block takes kPassCols consecutive columns of one block of M.
+template <bool INV>
+__global__ void __launch_bounds__(256) ntt_column_pass(uint32_t *a, int logN, int logM, int kp, TwTab T,
+                                                       TwTab TR, PrimeQ P) {
+  __shared__ uint32_t tile[kTileWords];
+  __shared__ uint32_t rt[kPassR / 2], rts[kPassR / 2];
+  const int R = 1 << kp, logNc = logM - kp;
+  const uint32_t Nc = 1u << logNc, M = 1u << logM;
+  const uint32_t q0 = blockIdx.x * kPassCols;            // first column of this block
+  const uint32_t bb = q0 >> logNc, c0 = q0 & (Nc - 1);
+  const size_t base = (size_t)bb * M + c0;
+  constexpr int ld = kPassCols + 1;
+  load_root_table(rt, rts, TR, R, logN);
+  for (int i = threadIdx.x; i < R * kPassCols; i += blockDim.x) {
+    const int m = i / kPassCols, cc = i % kPassCols;
+    uint32_t x = a[base + cc + (size_t)m * Nc];
+    if (INV) {
+      const uint32_t k = bitrev(m, kp);
+      const uint32_t e = (uint32_t)(((uint64_t)(c0 + cc) * k) & (M - 1)) << (logN - logM);
+      if (e) x = twiddle_apply(x, e, T, P.q);
+    }
+    tile[m * ld + cc] = x;
+  }
+  __syncthreads();
+  if (INV) tile_dit(tile, ld, kPassCols, R, rt, rts, P.q);
+  else tile_dif(tile, ld, kPassCols, R, rt, rts, P.q);
+  for (int i = threadIdx.x; i < R * kPassCols; i += blockDim.x) {
+    const int m = i / kPassCols, cc = i % kPassCols;
+    uint32_t x = tile[m * ld + cc];
+    if (!INV) {
+      const uint32_t k = bitrev(m, kp);
+      const uint32_t e = (uint32_t)(((uint64_t)(c0 + cc) * k) & (M - 1)) << (logN - logM);
+      if (e) x = twiddle_apply(x, e, T, P.q);
+    }
+    a[base + cc + (size_t)m * Nc] = x;
+  }
+}
+
+// The innermost pass on contiguous runs of R = 2^kp elements: forward R-point DIF, every entry to the n-th power,
+// inverse R-point DIT.  A block takes G = min(N, kPassR kPassCols) / R runs.
+__global__ void __launch_bounds__(256) ntt_inner_pow(uint32_t *a, int logN, int kp, uint32_t n, TwTab TF,
+                                                     TwTab TI, PrimeQ P) {
+  __shared__ uint32_t tile[kTileWords];
+  __shared__ uint32_t rf[kPassR / 2], rfs[kPassR / 2], ri[kPassR / 2], ris[kPassR / 2];
+  const int R = 1 << kp;
+  const uint32_t N = 1u << logN;
+  const int words = (int)min((uint32_t)(kPassR * kPassCols), N);
+  const int G = words / R, ld = G + 1;   // row stride G + 1: both the run-wise copies and the butterflies
+  const size_t base = (size_t)blockIdx.x * words;   // are free of shared-memory bank conflicts
+  load_root_table(rf, rfs, TF, R, logN);
+  load_root_table(ri, ris, TI, R, logN);
+  // tile[m * ld + g] = a[base + g R + m]: run g is a column of the tile
+  for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    const int g = i / R, m = i % R;
+    tile[m * ld + g] = a[base + i];
+  }
+  __syncthreads();
+  tile_dif(tile, ld, G, R, rf, rfs, P.q);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    const int g = i / R, m = i % R;
+    tile[m * ld + g] = powmod(tile[m * ld + g], n, P.q, P.mu);
+  }
+  __syncthreads();
+  tile_dit(tile, ld, G, R, ri, ris, P.q);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    const int g = i / R, m = i % R;
+    a[base + i] = tile[m * ld + g];
+  }
+}
+
 // residue of every output coefficient (packed descending lex, degree D = d n), times N^-1
 __global__ void gather_kernel(const uint32_t *a, int D, int B, uint32_t ninv, uint32_t *res, PrimeQ P) {
   const int n_out = tet(D + 1);
@@ -168,23 +292,58 @@ int polypow_primes(double log2_bound) {
   return 0;
 }
 
+// Twiddle table words of one prime and direction: lo and hi tables of 2^12 entries and the R-point roots, each with
+// its companion.
+constexpr size_t kTwWords = 2 * (4096 + 4096 + kPassR / 2);
+
 size_t polypow_scratch_words(int d, int n, int nprimes) {
   const int B = d * n + 1;
   uint32_t N = 1;
   while ((uint64_t)N < (uint64_t)B * B * B) N <<= 1;
-  return (size_t)N + (size_t)N + (size_t)nprimes * tet(d * n + 1) + tet(d + 1) + 64;
+  return (size_t)N + 2 * kTwWords + (size_t)nprimes * tet(d * n + 1) + tet(d + 1) + 64;
 }
+
+namespace {
+
+// Tables of w (forward) or w^-1 (inverse) for a length-N transform, in tab (kTwWords words).
+TwTab make_tables(uint32_t *tab, uint32_t w, uint32_t N, PrimeQ P, cudaStream_t st) {
+  TwTab T;
+  uint32_t *p = tab;
+  T.lo = p; T.los = p + 4096; p += 8192;
+  T.hi = p; T.his = p + 4096; p += 8192;
+  T.rt = p; T.rts = p + kPassR / 2;
+  const uint32_t R = N < (uint32_t)kPassR ? N : (uint32_t)kPassR;
+  const uint32_t nhi = N >> kTwLoBits ? N >> kTwLoBits : 1;
+  const uint32_t nlo = N < 4096u ? N : 4096u;
+  power_table_kernel<<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.lo), const_cast<uint32_t *>(T.los), nlo, w, 1, P);
+  power_table_kernel<<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.hi), const_cast<uint32_t *>(T.his), nhi, w, 4096, P);
+  // w_R^j for j < R / 2, stored at stride kPassR / R so that the R-point roots of every pass are rt[j * (kPassR / R)]
+  power_table_kernel<<<1, 128, 0, st>>>(const_cast<uint32_t *>(T.rt), const_cast<uint32_t *>(T.rts), R / 2, w,
+                                        N / R, P);
+  return T;
+}
+
+}  // namespace
 
 cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev, uint32_t *out, uint32_t *scratch,
                            cudaStream_t st) {
   const int B = d * n + 1, D = d * n;
   uint32_t N = 1;
-  while ((uint64_t)N < (uint64_t)B * B * B) N <<= 1;
+  int logN = 0;
+  while ((uint64_t)N < (uint64_t)B * B * B) { N <<= 1; ++logN; }
   const int n_out = tet(D + 1);
   uint32_t *a = scratch;
-  uint32_t *tw = a + N, *itw = tw + N / 2;
-  uint32_t *res = itw + N / 2;
+  uint32_t *twf = a + N, *twi = twf + kTwWords;
+  uint32_t *res = twi + kTwWords;
   const int grid = 152 * 8, block = 256;
+  // passes: the innermost takes min(8, logN) stages on contiguous runs; the rest, outermost first, up to 8 each
+  const int inner = logN < kPassMaxStages ? logN : kPassMaxStages;
+  int outer[4], n_outer = 0;
+  for (int rem = logN - inner; rem > 0;) {
+    const int kp = rem > kPassMaxStages ? kPassMaxStages : rem;
+    outer[n_outer++] = kp;
+    rem -= kp;
+  }
   CrtParams C;
   C.nprimes = nprimes;
   for (int j = 0; j < nprimes; ++j) {
@@ -196,12 +355,22 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
     const uint32_t w = (uint32_t)host_powmod(kRoot[j], (q - 1) / N, q);   // primitive N-th root
     const uint32_t wi = (uint32_t)host_powmod(w, q - 2, q);
     const uint32_t ninv = (uint32_t)host_powmod(N, q - 2, q);
-    twiddle_kernel<<<grid, block, 0, st>>>(tw, itw, N / 2, w, wi, P);
+    const TwTab TF = make_tables(twf, w, N, P, st);
+    const TwTab TI = make_tables(twi, wi, N, P, st);
     zero_kernel<<<grid, block, 0, st>>>(a, N);
     scatter_kernel<<<64, block, 0, st>>>(coeffs_dev, d, B, a, P);
-    for (uint32_t len = N; len >= 2; len >>= 1) dif_stage<<<grid, block, 0, st>>>(a, N, len / 2, N / len, tw, P);
-    pow_kernel<<<grid, block, 0, st>>>(a, N, (uint32_t)n, P);
-    for (uint32_t len = 2; len <= N; len <<= 1) dit_stage<<<grid, block, 0, st>>>(a, N, len / 2, N / len, itw, P);
+    // forward: outer passes on blocks of M = N, N / 2^kp0, ...; the inner pass fuses the powers and the inverse
+    int logM = logN;
+    for (int i = 0; i < n_outer; ++i) {
+      ntt_column_pass<false><<<(N >> outer[i]) / kPassCols, block, 0, st>>>(a, logN, logM, outer[i], TF, TF, P);
+      logM -= outer[i];
+    }
+    const uint32_t inner_words = N < (uint32_t)(kPassR * kPassCols) ? N : (uint32_t)(kPassR * kPassCols);
+    ntt_inner_pow<<<N / inner_words, block, 0, st>>>(a, logN, inner, (uint32_t)n, TF, TI, P);
+    for (int i = n_outer - 1; i >= 0; --i) {
+      logM += outer[i];
+      ntt_column_pass<true><<<(N >> outer[i]) / kPassCols, block, 0, st>>>(a, logN, logM, outer[i], TI, TI, P);
+    }
     gather_kernel<<<grid, block, 0, st>>>(a, D, B, ninv, res + (size_t)j * n_out, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
