@@ -540,7 +540,9 @@ struct Poly {
   static constexpr int idtaps_off = cnt_off + 16;
   // byte offset of each class in the class-ordered copy, indexed by sigma2 + p sigma3 + p^2 sigma4 (NCLS ints)
   static constexpr int sig_off = idtaps_off + ((tet(4 * P + 1) + 15) & ~15);
-  static constexpr int bytes = sig_off + 4 * NCLS;
+  // (s', t') of every packed index of a triangle of side d + 1 (s' | t' << 8), for the class-order copy
+  static constexpr int tri_off = sig_off + 4 * NCLS;
+  static constexpr int bytes = tri_off + ((2 * tri(d + 1) + 15) & ~15);
 };
 
 // Classes of degree k (kernel degree) in residue-class order: rho in [0,p)^4 with |rho| = d - p k.
@@ -746,36 +748,59 @@ __device__ __forceinline__ void poly_tables(unsigned char *ring) {
 }
 
 // Padded Delta (degree D) -> class order: class sigma holds Delta_sigma in packed order of B_{d-k}, starting at byte
-// sig_off[sigma] of `dc`.  One thread per 16-byte chunk of the padded Delta, read once and coalesced; each byte
-// (U, S, T) goes to class sigma = (e2, e3, e4) mod p at the packed index of (e - sigma) / p, where
-// (e2, e3, e4) = (U - S, S - T, T).  Within a chunk T advances by one, so e4 / p, e4 mod p, e3 / p and e3 mod p
-// advance incrementally.  The caller synchronises the CTA afterwards.
+// sig_off[sigma] of `dc`.  Slice U of the padded Delta (one coalesced copy into shared memory, the next slice in
+// flight meanwhile) holds, for every class with Su = U mod p (+ p, + 2p) and u' = (U - Su) / p <= d - k, the whole
+// slab u' of that class: the tri(u' + 1) bytes at packed indices tet(u') .. of Delta_sigma, contiguous in `dc`.
+// A warp writes one slab at a time, its lanes 32 consecutive bytes per store, reading byte (p s' + Ss, p t' + St)
+// of the staged slice for slab entry (s', t').  The two cube buffers of the ring stage the slices.  Ends with a
+// barrier.
 template <int P>
 __device__ __forceinline__ void delta_to_classes(const uint32_t *__restrict__ delta, uint32_t *__restrict__ dc,
-                                                 const Smem &sm, const unsigned char *ring) {
-  constexpr int D = Prime<P>::D;
-  const int *sig = reinterpret_cast<const int *>(ring + Poly<P>::sig_off);
+                                                 const Smem &sm, unsigned char *ring) {
+  using Q = Poly<P>;
+  constexpr int D = Prime<P>::D, d = Q::d;
+  constexpr int SLOT = 4 * chunk_prefix(D + 1);   // words of the largest slice
+  static_assert(2 * 4 * SLOT <= 2 * Q::CB, "two slices of Delta fit in the cube buffers");
+  const int *sig = reinterpret_cast<const int *>(ring + Q::sig_off);
+  uint16_t *tst = reinterpret_cast<uint16_t *>(ring + Q::tri_off);
+  uint32_t *stage = reinterpret_cast<uint32_t *>(ring);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
   uint8_t *db = reinterpret_cast<uint8_t *>(dc);
-  const int nchunks = sm.SW[D + 1] / 4;
-  for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
-    int U, S, c;
-    decode_form_chunk(k, D, sm.SW, U, S, c);
-    const uint4 v = *reinterpret_cast<const uint4 *>(delta + 4 * k);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    const int e2 = U - S, q2 = e2 / P, r2 = e2 - P * q2;
-    const int T0 = 16 * c;
-    int q4 = T0 / P, r4 = T0 - P * q4;                 // e4 = T
-    int q3 = (S - T0) / P, r3 = (S - T0) - P * q3;     // e3 = S - T (>= 0 while T <= S)
-#pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      if (T0 + b <= S) {
-        const int up = q2 + q3 + q4, sp = q3 + q4;
-        db[sig[r2 + P * r3 + P * P * r4] + tet(up) + tri(sp) + q4] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
-      }
-      if (++r4 == P) { r4 = 0; ++q4; }
-      if (--r3 < 0) { r3 = P - 1; --q3; }
-    }
+  for (int i = tid; i < tri(d + 1); i += blockDim.x) {
+    const int sp = (isqrt(8 * i + 1) - 1) >> 1;
+    tst[i] = (uint16_t)(sp | ((i - tri(sp)) << 8));
   }
+  auto fetch = [&](int U, int buf) {
+    const uint32_t *src = delta + sm.SW[U];
+    uint32_t *dst = stage + buf * SLOT;
+    for (int k = tid; k < chunk_prefix(U + 1); k += blockDim.x) cp_async16(dst + 4 * k, src + 4 * k, true);
+  };
+  fetch(0, 0);
+  cp_async_commit();
+  for (int U = 0; U <= D; ++U) {
+    if (U + 1 <= D) fetch(U + 1, (U + 1) & 1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::);
+    __syncthreads();   // slice U is staged for every thread (and the table above is written)
+    const uint8_t *sl = reinterpret_cast<const uint8_t *>(stage + (U & 1) * SLOT);
+    // candidate classes: Su in {U mod p, + p, + 2p}, then sigma4 and sigma3 (sigma2 = Su - sigma3 - sigma4)
+    const int su0 = U % P;
+    for (int cand = warp; cand < 3 * P * P; cand += nwarps) {
+      const int Su = su0 + P * (cand / (P * P)), s3 = (cand / P) % P, s4 = cand % P, s2 = Su - s3 - s4;
+      if (Su > U || s2 < 0 || s2 >= P) continue;
+      const int s1 = ((D - Su) % P + P) % P, k = (s1 + Su) / P, up = (U - Su) / P;
+      if (up > d - k) continue;
+      const int Ss = s3 + s4, St = s4;
+      uint8_t *dst = db + sig[s2 + P * s3 + P * P * s4] + tet(up);
+      for (int i = lane; i < tri(up + 1); i += 32) {
+        const int x = tst[i], sp = x & 255, tp = x >> 8;
+        dst[i] = sl[4 * colw(P * sp + Ss) + P * tp + St];
+      }
+    }
+    __syncthreads();   // slot U & 1 may be refilled
+  }
+  cp_async_wait_all();
+  __syncthreads();
 }
 
 // Products of one class: acc[o] += sum over the taps c' in B_K of g_rho[c'] Delta_sigma[r_o - c'], reading

@@ -108,28 +108,32 @@ __global__ void power_table_kernel(uint32_t *table, uint32_t *comp, uint32_t n, 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
 
 // R-point DIF (natural in, bit-reversed out) on the columns of a shared tile: element m of column cc at
-// tile[m * ld + cc], ncol columns; twiddles w_R^j from rt (stage of length len uses w_R^(j R / len)).
-__device__ __forceinline__ void tile_dif(uint32_t *tile, int ld, int ncol, int R, const uint32_t *rt,
+// tile[m * ld + cc], 2^lgcol columns, R = 2^kp; twiddles w_R^j from rt (stage of length len uses w_R^(j R / len)).
+// Index arithmetic by shifts and masks (every extent is a power of two).
+__device__ __forceinline__ void tile_dif(uint32_t *tile, int ld, int lgcol, int kp, const uint32_t *rt,
                                          const uint32_t *rts, uint32_t q) {
-  for (int len = R; len >= 2; len >>= 1) {
-    const int h = len >> 1, ts = R / len;
-    for (int t = threadIdx.x; t < ncol * (R >> 1); t += blockDim.x) {
-      const int cc = t % ncol, b = t / ncol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+  const int R = 1 << kp, nb = 1 << (lgcol + kp - 1);
+  for (int lglen = kp; lglen >= 1; --lglen) {
+    const int h = 1 << (lglen - 1), lgts = kp - lglen;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      const int cc = t & ((1 << lgcol) - 1), b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
       const uint32_t u = tile[i0 * ld + cc], v = tile[i1 * ld + cc];
       tile[i0 * ld + cc] = addmod(u, v, q);
-      tile[i1 * ld + cc] = shoup_mul(submod(u, v, q), rt[j * ts], rts[j * ts], q);
+      tile[i1 * ld + cc] = shoup_mul(submod(u, v, q), rt[j << lgts], rts[j << lgts], q);
     }
     __syncthreads();
   }
+  (void)R;
 }
 // R-point inverse DIT (bit-reversed in, natural out), twiddles w_R^-j
-__device__ __forceinline__ void tile_dit(uint32_t *tile, int ld, int ncol, int R, const uint32_t *rt,
+__device__ __forceinline__ void tile_dit(uint32_t *tile, int ld, int lgcol, int kp, const uint32_t *rt,
                                          const uint32_t *rts, uint32_t q) {
-  for (int len = 2; len <= R; len <<= 1) {
-    const int h = len >> 1, ts = R / len;
-    for (int t = threadIdx.x; t < ncol * (R >> 1); t += blockDim.x) {
-      const int cc = t % ncol, b = t / ncol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
-      const uint32_t u = tile[i0 * ld + cc], v = shoup_mul(tile[i1 * ld + cc], rt[j * ts], rts[j * ts], q);
+  const int nb = 1 << (lgcol + kp - 1);
+  for (int lglen = 1; lglen <= kp; ++lglen) {
+    const int h = 1 << (lglen - 1), lgts = kp - lglen;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      const int cc = t & ((1 << lgcol) - 1), b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+      const uint32_t u = tile[i0 * ld + cc], v = shoup_mul(tile[i1 * ld + cc], rt[j << lgts], rts[j << lgts], q);
       tile[i0 * ld + cc] = addmod(u, v, q);
       tile[i1 * ld + cc] = submod(u, v, q);
     }
@@ -173,8 +177,10 @@ __global__ void __launch_bounds__(256) ntt_column_pass(uint32_t *a, int logN, in
     tile[m * ld + cc] = x;
   }
   __syncthreads();
-  if (INV) tile_dit(tile, ld, kPassCols, R, rt, rts, P.q);
-  else tile_dif(tile, ld, kPassCols, R, rt, rts, P.q);
+  constexpr int lgcols = 5;
+  static_assert((1 << lgcols) == kPassCols, "columns per block");
+  if (INV) tile_dit(tile, ld, lgcols, kp, rt, rts, P.q);
+  else tile_dif(tile, ld, lgcols, kp, rt, rts, P.q);
   for (int i = threadIdx.x; i < R * kPassCols; i += blockDim.x) {
     const int m = i / kPassCols, cc = i % kPassCols;
     uint32_t x = tile[m * ld + cc];
@@ -194,27 +200,27 @@ __global__ void __launch_bounds__(256) ntt_inner_pow(uint32_t *a, int logN, int 
   __shared__ uint32_t tile[kTileWords];
   __shared__ uint32_t rf[kPassR / 2], rfs[kPassR / 2], ri[kPassR / 2], ris[kPassR / 2];
   const int R = 1 << kp;
-  const uint32_t N = 1u << logN;
-  const int words = (int)min((uint32_t)(kPassR * kPassCols), N);
-  const int G = words / R, ld = G + 1;   // row stride G + 1: both the run-wise copies and the butterflies
+  const int lgw = logN < kPassMaxStages + 5 ? logN : kPassMaxStages + 5;   // words = min(kPassR kPassCols, N)
+  const int words = 1 << lgw, lgg = lgw - kp;
+  const int ld = (1 << lgg) + 1;   // row stride G + 1: both the run-wise copies and the butterflies
   const size_t base = (size_t)blockIdx.x * words;   // are free of shared-memory bank conflicts
   load_root_table(rf, rfs, TF, R, logN);
   load_root_table(ri, ris, TI, R, logN);
   // tile[m * ld + g] = a[base + g R + m]: run g is a column of the tile
   for (int i = threadIdx.x; i < words; i += blockDim.x) {
-    const int g = i / R, m = i % R;
+    const int g = i >> kp, m = i & (R - 1);
     tile[m * ld + g] = a[base + i];
   }
   __syncthreads();
-  tile_dif(tile, ld, G, R, rf, rfs, P.q);
+  tile_dif(tile, ld, lgg, kp, rf, rfs, P.q);
   for (int i = threadIdx.x; i < words; i += blockDim.x) {
-    const int g = i / R, m = i % R;
+    const int g = i >> kp, m = i & (R - 1);
     tile[m * ld + g] = powmod(tile[m * ld + g], n, P.q, P.mu);
   }
   __syncthreads();
-  tile_dit(tile, ld, G, R, ri, ris, P.q);
+  tile_dit(tile, ld, lgg, kp, ri, ris, P.q);
   for (int i = threadIdx.x; i < words; i += blockDim.x) {
-    const int g = i / R, m = i % R;
+    const int g = i >> kp, m = i & (R - 1);
     a[base + i] = tile[m * ld + g];
   }
 }
