@@ -508,8 +508,31 @@ __host__ __device__ constexpr int theta_r_words() {
   for (int u = 0; u <= 4 * (P - 1); ++u) r += rcolw(u + 1);
   return r;
 }
-// Theta runs by residue classes at p <= 7 (theta_poly below) and gathers from the guarded copy at p >= 11, whose
-// padded cube of one class would not fit in shared memory.
+// Theta at p = 7 in the chain power mode streams Delta slice by slice through shared memory (two guarded slice
+// slots, theta_stream): the copy of Delta into class order that theta_poly reads would add a round trip of the whole
+// 0.8 MB Delta through device memory per quartic.  At p <= 5, and for the identity power mode at p <= 7 (which forms
+// Delta in class order directly), theta runs by residue classes; at p >= 11 it gathers from a guarded copy.
+template <int P>
+__host__ __device__ constexpr bool theta_streams() { return P == 7; }
+// a slice slot: columns 0 .. D with the guards of the guarded layout
+template <int P>
+__host__ __device__ constexpr int theta_slot_words() { return kThetaGuardWords * (4 * P * (P - 1) + 2) + colw(4 * P * (P - 1) + 1); }
+// slice slots of the streamed theta (prefetch distance slots - 1)
+template <int P>
+__host__ __device__ constexpr int theta_nslots() { return 2; }
+// word offset of the slice slots in the ring (16-byte aligned for cp.async)
+template <int P>
+__host__ __device__ constexpr int theta_slots_off() { return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3; }
+// ring words of the streamed theta: reversed g columns and their slice table, the slice slots, int32 accumulators,
+// the chunk-to-slot table and the unpacked output coordinates
+template <int P>
+__host__ __device__ constexpr int theta_stream_ring_words() {
+  constexpr int d = 4 * (P - 1), D = 4 * P * (P - 1), ld = tet(d + 1);
+  return theta_slots_off<P>() + theta_nslots<P>() * theta_slot_words<P>() + ld + chunk_prefix(D + 1) + ld + D + 1;
+}
+
+// Theta by residue classes (theta_poly below) is built for p <= 7; at p >= 11 the padded cube of one class would not
+// fit in shared memory.
 template <int P>
 __host__ __device__ constexpr bool theta_by_classes() { return P <= 7; }
 
@@ -521,6 +544,8 @@ __host__ __device__ constexpr bool theta_by_classes() { return P <= 7; }
 // classes hold every coefficient of g once and every coefficient of Delta once, and the MACs add up to the theta
 // matrix's nonzeros.  Each class is a product with a kernel of at most 20 taps, computed on a zero-padded cube of
 // Delta_sigma in shared memory, so no term needs a bounds check.
+constexpr int kPolyStages = 4;   // class-data staging slots of theta_poly (prefetch distance 3 classes)
+
 template <int P>
 struct Poly {
   static constexpr int d = 4 * (P - 1), ld = tet(d + 1);
@@ -540,9 +565,13 @@ struct Poly {
   static constexpr int idtaps_off = cnt_off + 16;
   // byte offset of each class in the class-ordered copy, indexed by sigma2 + p sigma3 + p^2 sigma4 (NCLS ints)
   static constexpr int sig_off = idtaps_off + ((tet(4 * P + 1) + 15) & ~15);
-  // (s', t') of every packed index of a triangle of side d + 1 (s' | t' << 8), for the class-order copy
-  static constexpr int tri_off = sig_off + 4 * NCLS;
-  static constexpr int bytes = tri_off + ((2 * tri(d + 1) + 15) & ~15);
+  // staging slots of theta_poly's class stream (kPolyStages slots of the largest class; 16-byte cp.async targets)
+  static constexpr int stage_off = sig_off + ((4 * NCLS + 15) & ~15);
+  static constexpr int bytes = stage_off + kPolyStages * ((ld + 15) & ~15);
+  // every region starts on a 16-byte boundary (uint4 stores, int4 records, cp.async)
+  static_assert(taps_off % 16 == 0 && tapsrc_off % 16 == 0 && cubeaddr_off % 16 == 0 && cls_off % 16 == 0 &&
+                    cnt_off % 16 == 0 && idtaps_off % 16 == 0 && sig_off % 16 == 0 && stage_off % 16 == 0,
+                "16-byte aligned ring regions");
 };
 
 // Classes of degree k (kernel degree) in residue-class order: rho in [0,p)^4 with |rho| = d - p k.
@@ -567,7 +596,9 @@ inline size_t theta_class_words(int p) {
 template <int P>
 __host__ __device__ constexpr int theta_ring_words() {
   if constexpr (theta_by_classes<P>()) {
-    return (Poly<P>::bytes + 3) / 4;
+    constexpr int poly = (Poly<P>::bytes + 3) / 4;
+    if constexpr (theta_streams<P>()) return poly > theta_stream_ring_words<P>() ? poly : theta_stream_ring_words<P>();
+    else return poly;
   } else {
     return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3;   // reversed g columns and their slice table
   }
@@ -680,6 +711,172 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
   return __syncthreads_or(any ? 1 : 0) != 0;
 }
 
+// Up to four g columns s_c = sc0 .. sc1 of a streamed theta round, all of NW words (sc0 / 4 == sc1 / 4), for the
+// output r = (u_r, s_r, t_r) of this lane: each column s_c inside the lane's range [lo, hi] adds the lane's Delta
+// window (NW + 1 words of the guarded slot, shifted to the window's first byte) against the NW words of g's
+// reversed column s_c, which are the same for every lane.  ebase = p s_r + 2(p-1), so the Delta column is
+// e_s = ebase - s_c; tbase = p t_r + (p-1), the window's last byte in that column.  All loads of the four columns
+// are issued before the first product.
+template <int P, int NW>
+__device__ __forceinline__ unsigned theta_seg(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rb,
+                                              const int *__restrict__ gofs, int sc0, int sc1, int lo, int hi,
+                                              int ebase, int tbase, unsigned a) {
+  uint32_t dv[4][NW + 1], rv[4][NW];
+  unsigned sh[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int sc = sc0 + j;
+    const bool in = sc <= sc1;
+    const bool on = in && sc >= lo && sc <= hi;
+    const int byte = on ? gofs[ebase - sc] + tbase - sc : 0;
+    sh[j] = 8u * (unsigned)(byte & 3);
+    const uint32_t *dw = slot + (byte >> 2);
+#pragma unroll
+    for (int k = 0; k <= NW; ++k) dv[j][k] = on ? dw[k] : 0u;
+    const uint32_t *rw = Rb + rcolw(sc);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) rv[j][k] = in ? rw[k] : 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < NW; ++k) a = __dp4a(__funnelshift_r(dv[j][k], dv[j][k + 1], sh[j]), rv[j][k], a);
+  return a;
+}
+
+// One theta step with Delta (padded, degree D, global memory) streamed through shared memory (p = 7).  Round e_u
+// copies slice e_u into a guarded slot (16-byte cp.async, double buffered) and serves every output slice u_r whose
+// g slice u_c = p u_r + 3(p-1) - e_u exists, in blocks of 32 consecutive outputs (one per lane) that sum over the
+// g columns in registers; each round's sums go to shared int32 accumulators.  Every Delta byte is read from global
+// memory once per step.  Returns whether some output is nonzero (same value in every thread).
+template <int P>
+__device__ __noinline__ bool theta_stream(const uint32_t *__restrict__ delta, const Smem &sm,
+                                          const uint8_t *__restrict__ g, uint8_t *__restrict__ gn, uint32_t *ring) {
+  static_assert(P <= 7, "g columns of at most 7 words");
+  using Pr = Prime<P>;
+  constexpr int d = Pr::d, D = Pr::D, ld = Pr::ld;
+  constexpr int SLOT = theta_slot_words<P>();
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
+  uint32_t *R = ring;
+  int *RSW = reinterpret_cast<int *>(ring + theta_r_words<P>());
+  constexpr int NS = theta_nslots<P>();
+  uint32_t *slots = ring + theta_slots_off<P>();                        // NS x SLOT, 16-byte aligned
+  int *acc = reinterpret_cast<int *>(slots + NS * SLOT);
+  int *ctab = acc + ld;                                                 // flat chunk of a slice -> slot word
+  uint32_t *rst = reinterpret_cast<uint32_t *>(ctab + chunk_prefix(D + 1));   // output r -> ur | sr << 8 | tr << 16
+  int *gofs = reinterpret_cast<int *>(rst + ld);                        // column e_s -> byte offset in a slot
+  for (int es = tid; es <= D; es += nthreads) gofs[es] = 4 * (kThetaGuardWords * (es + 1) + colw(es));
+  if (tid == 0) {
+    int a = 0;
+    for (int u = 0; u <= d + 1; ++u) { RSW[u] = a; a += rcolw(u + 1); }
+  }
+  for (int i = tid; i < NS * SLOT; i += nthreads) slots[i] = 0u;
+  for (int i = tid; i < ld; i += nthreads) {
+    acc[i] = 0;
+    int u, s, t;
+    decode_packed(i, u, s, t, d);
+    rst[i] = (uint32_t)u | ((uint32_t)s << 8) | ((uint32_t)t << 16);
+  }
+  for (int k = tid; k < chunk_prefix(D + 1); k += nthreads) {
+    int es, c;
+    decode_chunk(k, es, c);
+    ctab[k] = kThetaGuardWords * (es + 1) + colw(es) + 4 * c;
+  }
+  __syncthreads();
+  for (int i = tid; i < theta_r_words<P>(); i += nthreads) {
+    int u = 0;
+    while (RSW[u + 1] <= i) ++u;
+    const int rem = i - RSW[u];
+    int sc = 0;
+    while (rcolw(sc + 1) <= rem) ++sc;
+    const int k = rem - rcolw(sc);
+    const uint8_t *gcol = g + tet(u) + tri(sc);
+    uint32_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * k + b;
+      if (j <= sc) w |= (uint32_t)gcol[sc - j] << (8 * b);
+    }
+    R[i] = w;
+  }
+  auto fetch = [&](int eu, int buf) {
+    uint32_t *dst = slots + buf * SLOT;
+    const uint32_t *src = delta + sm.SW[eu];
+    const int n = chunk_prefix(eu + 1);
+    for (int k = tid; k < n; k += nthreads) cp_async16(dst + ctab[k], src + 4 * k, true);
+  };
+  // slices 0 .. NS-2 in flight; round e_u waits for its own slice, then refills the slot round e_u - 1 used
+  for (int e = 0; e < NS - 1; ++e) {
+    if (e <= D) fetch(e, e);
+    cp_async_commit();
+  }
+  for (int eu = 0; eu <= D; ++eu) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));
+    __syncthreads();   // slot eu % NS is complete for every thread; slot (eu - 1) % NS is no longer read
+    if (eu + NS - 1 <= D) fetch(eu + NS - 1, (eu + NS - 1) % NS);
+    cp_async_commit();
+    const uint32_t *slot = slots + (eu % NS) * SLOT;
+    // output slices with u_c = p u_r + 3(p-1) - e_u in [0, d]
+    const int base = eu - 3 * (P - 1);
+    const int ur_lo = max(0, (base + P - 1) / P);
+    const int ur_hi = min(d, base + d >= 0 ? (base + d) / P : -1);
+    if (ur_lo > ur_hi) continue;
+    // blocks of 32 consecutive outputs of a slice u_r, one warp each (lane = output): a lane sums, over every g
+    // column s_c whose Delta column e_s = p s_r + 2(p-1) - s_c lies in slice e_u, in registers, and adds the total
+    // to its output once per round; the warp runs the union of its lanes' column ranges, four columns at a time
+    int nblocks = 0;
+    for (int ur = ur_lo; ur <= ur_hi; ++ur) nblocks += (tri(ur + 1) + 31) >> 5;
+    for (int blk = warp; blk < nblocks; blk += nwarps) {
+      int ur = ur_lo, b = blk;
+      for (;;) {
+        const int nb = (tri(ur + 1) + 31) >> 5;
+        if (b < nb) break;
+        b -= nb;
+        ++ur;
+      }
+      const int uc = P * ur - base;   // in [0, d] for ur in [ur_lo, ur_hi]
+      const int i = 32 * b + lane;
+      const bool act = i < tri(ur + 1);
+      const int r = tet(ur) + i;
+      int lo = 1 << 30, hi = -1, ebase = 0, tbase = 0;
+      if (act) {
+        const uint32_t x = rst[r];
+        ebase = P * (int)((x >> 8) & 255u) + 2 * (P - 1);
+        tbase = P * (int)(x >> 16) + (P - 1);
+        lo = max(0, ebase - eu);   // e_s <= e_u
+        hi = min(uc, ebase);       // e_s >= 0
+      }
+      const int wlo = __reduce_min_sync(0xffffffffu, lo), whi = __reduce_max_sync(0xffffffffu, hi);
+      if (wlo > whi) continue;
+      const uint32_t *Rb = R + RSW[uc];
+      unsigned a = 0;
+      for (int q = wlo >> 2; q <= (whi >> 2); ++q) {
+        const int sc0 = max(wlo, 4 * q), sc1 = min(whi, 4 * q + 3);
+        switch (q) {   // words of g's reversed column: s_c / 4 + 1 <= p
+          case 0: a = theta_seg<P, 1>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 1: a = theta_seg<P, 2>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 2: a = theta_seg<P, 3>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 3: a = theta_seg<P, 4>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 4: a = theta_seg<P, 5>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          case 5: a = theta_seg<P, 6>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+          default: a = theta_seg<P, 7>(slot, Rb, gofs, sc0, sc1, lo, hi, ebase, tbase, a); break;
+        }
+      }
+      if (act && a != 0u) atomicAdd(acc + r, (int)a);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  bool any = false;
+  for (int r = tid; r < ld; r += nthreads) {
+    const int v = acc[r] % P;
+    gn[r] = (uint8_t)v;
+    any |= v != 0;
+  }
+  return __syncthreads_or(any ? 1 : 0) != 0;
+}
+
 // Class records of theta_poly (ring, Poly<P>::cls_off): x = byte offset of Delta_sigma in the class-ordered copy,
 // y = offset of g_rho's taps in the tap arrays, z = k | Su << 8 | Ss << 16 | St << 24 where (Su, Ss, St) is sigma in
 // (u, s, t) coordinates (Delta_sigma[u', s', t'] = Delta[p u' + Su, p s' + Ss, p t' + St]), w = offset of the class's
@@ -748,59 +945,36 @@ __device__ __forceinline__ void poly_tables(unsigned char *ring) {
 }
 
 // Padded Delta (degree D) -> class order: class sigma holds Delta_sigma in packed order of B_{d-k}, starting at byte
-// sig_off[sigma] of `dc`.  Slice U of the padded Delta (one coalesced copy into shared memory, the next slice in
-// flight meanwhile) holds, for every class with Su = U mod p (+ p, + 2p) and u' = (U - Su) / p <= d - k, the whole
-// slab u' of that class: the tri(u' + 1) bytes at packed indices tet(u') .. of Delta_sigma, contiguous in `dc`.
-// A warp writes one slab at a time, its lanes 32 consecutive bytes per store, reading byte (p s' + Ss, p t' + St)
-// of the staged slice for slab entry (s', t').  The two cube buffers of the ring stage the slices.  Ends with a
-// barrier.
+// sig_off[sigma] of `dc`.  One thread per 16-byte chunk of the padded Delta, read once and coalesced; each byte
+// (U, S, T) goes to class sigma = (e2, e3, e4) mod p at the packed index of (e - sigma) / p, where
+// (e2, e3, e4) = (U - S, S - T, T).  Within a chunk T advances by one, so e4 / p, e4 mod p, e3 / p and e3 mod p
+// advance incrementally.  The caller synchronises the CTA afterwards.
 template <int P>
 __device__ __forceinline__ void delta_to_classes(const uint32_t *__restrict__ delta, uint32_t *__restrict__ dc,
-                                                 const Smem &sm, unsigned char *ring) {
-  using Q = Poly<P>;
-  constexpr int D = Prime<P>::D, d = Q::d;
-  constexpr int SLOT = 4 * chunk_prefix(D + 1);   // words of the largest slice
-  static_assert(2 * 4 * SLOT <= 2 * Q::CB, "two slices of Delta fit in the cube buffers");
-  const int *sig = reinterpret_cast<const int *>(ring + Q::sig_off);
-  uint16_t *tst = reinterpret_cast<uint16_t *>(ring + Q::tri_off);
-  uint32_t *stage = reinterpret_cast<uint32_t *>(ring);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+                                                 const Smem &sm, const unsigned char *ring) {
+  constexpr int D = Prime<P>::D;
+  const int *sig = reinterpret_cast<const int *>(ring + Poly<P>::sig_off);
   uint8_t *db = reinterpret_cast<uint8_t *>(dc);
-  for (int i = tid; i < tri(d + 1); i += blockDim.x) {
-    const int sp = (isqrt(8 * i + 1) - 1) >> 1;
-    tst[i] = (uint16_t)(sp | ((i - tri(sp)) << 8));
-  }
-  auto fetch = [&](int U, int buf) {
-    const uint32_t *src = delta + sm.SW[U];
-    uint32_t *dst = stage + buf * SLOT;
-    for (int k = tid; k < chunk_prefix(U + 1); k += blockDim.x) cp_async16(dst + 4 * k, src + 4 * k, true);
-  };
-  fetch(0, 0);
-  cp_async_commit();
-  for (int U = 0; U <= D; ++U) {
-    if (U + 1 <= D) fetch(U + 1, (U + 1) & 1);
-    cp_async_commit();
-    asm volatile("cp.async.wait_group 1;\n" ::);
-    __syncthreads();   // slice U is staged for every thread (and the table above is written)
-    const uint8_t *sl = reinterpret_cast<const uint8_t *>(stage + (U & 1) * SLOT);
-    // candidate classes: Su in {U mod p, + p, + 2p}, then sigma4 and sigma3 (sigma2 = Su - sigma3 - sigma4)
-    const int su0 = U % P;
-    for (int cand = warp; cand < 3 * P * P; cand += nwarps) {
-      const int Su = su0 + P * (cand / (P * P)), s3 = (cand / P) % P, s4 = cand % P, s2 = Su - s3 - s4;
-      if (Su > U || s2 < 0 || s2 >= P) continue;
-      const int s1 = ((D - Su) % P + P) % P, k = (s1 + Su) / P, up = (U - Su) / P;
-      if (up > d - k) continue;
-      const int Ss = s3 + s4, St = s4;
-      uint8_t *dst = db + sig[s2 + P * s3 + P * P * s4] + tet(up);
-      for (int i = lane; i < tri(up + 1); i += 32) {
-        const int x = tst[i], sp = x & 255, tp = x >> 8;
-        dst[i] = sl[4 * colw(P * sp + Ss) + P * tp + St];
+  const int nchunks = sm.SW[D + 1] / 4;
+  for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
+    int U, S, c;
+    decode_form_chunk(k, D, sm.SW, U, S, c);
+    const uint4 v = *reinterpret_cast<const uint4 *>(delta + 4 * k);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const int e2 = U - S, q2 = e2 / P, r2 = e2 - P * q2;
+    const int T0 = 16 * c;
+    int q4 = T0 / P, r4 = T0 - P * q4;                 // e4 = T
+    int q3 = (S - T0) / P, r3 = (S - T0) - P * q3;     // e3 = S - T (>= 0 while T <= S)
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      if (T0 + b <= S) {
+        const int up = q2 + q3 + q4, sp = q3 + q4;
+        db[sig[r2 + P * r3 + P * P * r4] + tet(up) + tri(sp) + q4] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
       }
+      if (++r4 == P) { r4 = 0; ++q4; }
+      if (--r3 < 0) { r3 = P - 1; --q3; }
     }
-    __syncthreads();   // slot U & 1 may be refilled
   }
-  cp_async_wait_all();
-  __syncthreads();
 }
 
 // Products of one class: acc[o] += sum over the taps c' in B_K of g_rho[c'] Delta_sigma[r_o - c'], reading
@@ -823,29 +997,54 @@ __device__ __forceinline__ void poly_macs(const uint8_t *cube, const uint8_t *tp
 }
 
 // One theta step by residue classes (p <= 7): g (shared, packed) -> gn.  `dc` holds Delta in class order
-// (delta_to_classes) and poly_tables has run.  Classes stream through two cubes in shared memory: class j + 1's
-// words are loaded while class j is multiplied, then scattered into the other cube, with one barrier per class.
-// Cube positions outside B_d are zero from the start; when the degree d - k of the classes drops, the cube's slab
-// of the old degree is cleared, so each cube always holds zeros outside its current class's cone.  Returns whether
-// some output is nonzero (same value in every thread).
+// (delta_to_classes) and poly_tables has run.  Class data streams from `dc` into a ring of kPolyStages shared-memory
+// slots by 16-byte cp.async, kPolyStages - 1 classes ahead; each thread then scatters the chunks it copied itself
+// into the cube that the class is multiplied from, so a copy needs no barrier, and one barrier per class separates
+// a cube's scatter from its products.  Two cubes alternate.  Cube positions outside B_d are zero from the start;
+// when the degree d - k of the classes drops, the cube's slab of the old degree is cleared, so each cube always
+// holds zeros outside its current class's cone.  Returns whether some output is nonzero (same value in every
+// thread).
 template <int P>
 __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const uint8_t *__restrict__ g,
                                         uint8_t *__restrict__ gn, unsigned char *ring) {
   using Q = Poly<P>;
-  // every thread of the CTA (kThreads of them) owns NOUT outputs and NWT words of a class
-  constexpr int d = Q::d, ld = Q::ld, C = Q::C, NOUT = Q::NOUT;
-  constexpr int NW = (ld + 3) / 4;                           // words of the largest class
-  constexpr int NWT = (NW + kThreads - 1) / kThreads;        // words per thread
+  constexpr int d = Q::d, ld = Q::ld, C = Q::C, NOUT = Q::NOUT, NS = kPolyStages;
+  constexpr int SB = (ld + 15) & ~15;   // bytes of a staging slot (the largest class)
   const int tid = threadIdx.x, nthreads = blockDim.x;
   uint8_t *cube0 = ring;
   uint8_t *taps = ring + Q::taps_off;
   const uint16_t *tapsrc = reinterpret_cast<const uint16_t *>(ring + Q::tapsrc_off);
   const uint16_t *cubeaddr = reinterpret_cast<const uint16_t *>(ring + Q::cubeaddr_off);
   const int4 *cls = reinterpret_cast<const int4 *>(ring + Q::cls_off);
+  uint8_t *stg = ring + Q::stage_off;
   // taps of every class in class order, and both cubes cleared
   for (int i = tid; i < ld; i += nthreads) taps[i] = g[tapsrc[i]];
   for (int i = tid; i < 2 * Q::CB / 16; i += nthreads) reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
+  // class j -> slot j % NS: this thread copies chunks tid, tid + nthreads, .. of it
+  auto stage = [&](int j) {
+    if (j < Q::NCLS) {
+      const int4 c = cls[j];
+      const int n16 = (tet(d - (c.z & 255) + 1) + 15) >> 4;
+      uint32_t *dst = reinterpret_cast<uint32_t *>(stg + (j % NS) * SB);
+      for (int i = tid; i < n16; i += nthreads) cp_async16(dst + 4 * i, dc + c.x / 4 + 4 * i, true);
+    }
+    cp_async_commit();
+  };
+  // scatter this thread's chunks of class j (staged) into `cube`
+  auto scatter = [&](int j, uint8_t *cube) {
+    const int4 c = cls[j];
+    const int len = tet(d - (c.z & 255) + 1);
+    const uint8_t *src = stg + (j % NS) * SB;
+    for (int i = tid; 16 * i < len; i += nthreads) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(src + 16 * i);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int b = 0; b < 16; ++b)
+        if (16 * i + b < len) cube[cubeaddr[16 * i + b]] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
+    }
+  };
+  for (int j = 0; j < NS - 1; ++j) stage(j);
+  __syncthreads();   // cubes cleared and taps written
   // output addresses: r_o = tid + kThreads o; threads past B_d read the cube around output (0, 0, 0), and drop it
   int a[NOUT], acc[NOUT];
 #pragma unroll
@@ -854,38 +1053,16 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
     a[o] = r < ld ? (int)cubeaddr[r] : Q::pad * (C * C + C + 1);
     acc[o] = 0;
   }
-  // class 0 into cube 0
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));   // class 0 is staged
+  scatter(0, cube0);
   int degb[2] = {d, d};   // degree of the cone each cube was last filled with (uniform)
-  {
-    const int4 c = cls[0];
-    const int len = tet(d - (c.z & 255) + 1);
-    for (int w = tid; 4 * w < len; w += nthreads) {
-      const uint32_t word = dc[c.x / 4 + w];
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (4 * w + b < len) cube0[cubeaddr[4 * w + b]] = (uint8_t)(word >> (8 * b));
-    }
-  }
   __syncthreads();
   for (int j = 0; j < Q::NCLS; ++j) {
     const int4 c = cls[j];
     const int k = c.z & 255;
-    uint8_t *cube = cube0 + (j & 1) * Q::CB;
-    uint8_t *next = cube0 + ((j + 1) & 1) * Q::CB;
-    // class j + 1's words in flight while class j is multiplied
-    uint32_t pre[NWT];
-    int nlen = 0, nk = 0;
-    if (j + 1 < Q::NCLS) {
-      const int4 cn = cls[j + 1];
-      nk = cn.z & 255;
-      nlen = tet(d - nk + 1);
-#pragma unroll
-      for (int q = 0; q < NWT; ++q) {
-        const int w = tid + kThreads * q;
-        pre[q] = 4 * w < nlen ? dc[cn.x / 4 + w] : 0u;
-      }
-    }
+    stage(j + NS - 1);   // into the slot class j - 1 left (scattered by this thread two classes ago)
     const uint8_t *tp = taps + c.y;
+    const uint8_t *cube = cube0 + (j & 1) * Q::CB;
     switch (k) {
       case 0: poly_macs<P, 0>(cube, tp, a, acc); break;
       case 1: poly_macs<P, 1>(cube, tp, a, acc); break;
@@ -895,21 +1072,18 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
     if (j + 1 < Q::NCLS) {
       // the other cube: clear the slab its previous class left beyond the new degree, then scatter class j + 1
       const int b = (j + 1) & 1;
-      const int nd = d - nk;
+      uint8_t *next = cube0 + b * Q::CB;
+      const int nd = d - (cls[j + 1].z & 255);
       if (degb[b] > nd) {
         for (int i = tet(nd + 1) + tid; i < tet(degb[b] + 1); i += nthreads) next[cubeaddr[i]] = 0;
         degb[b] = nd;
       }
-#pragma unroll
-      for (int q = 0; q < NWT; ++q) {
-        const int w = tid + kThreads * q;
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb)
-          if (4 * w + bb < nlen) next[cubeaddr[4 * w + bb]] = (uint8_t)(pre[q] >> (8 * bb));
-      }
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));   // class j + 1 is staged
+      scatter(j + 1, next);
     }
     __syncthreads();
   }
+  cp_async_wait_all();
   bool any = false;
 #pragma unroll
   for (int o = 0; o < NOUT; ++o) {
@@ -1413,14 +1587,16 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   }
   if (DEBUG && !in_classes)
     for (int k = tid; k < sm.SW[Pr::D + 1]; k += blockDim.x) dbg.delta[k] = delta[k];
-  // A6 + A7.  Theta reads a copy of Delta built in the buffer that does not hold it: in residue-class order at
-  // p <= 7 (theta_poly), guarded at p >= 11 (theta_gather)
+  // A6 + A7.  Theta: by residue classes at p <= 5 and for the identity mode at p = 7 (Delta in class order, copied
+  // into the buffer that does not hold Delta unless the identity mode wrote it so), streamed from the padded Delta
+  // at p = 7 otherwise, and gathered from a guarded copy at p >= 11
   uint32_t *dg = delta == bufA ? bufB : bufA;
   unsigned char *ringb = reinterpret_cast<unsigned char *>(ring);
+  const bool by_classes = theta_by_classes<P>() && (!theta_streams<P>() || in_classes);
   if constexpr (theta_by_classes<P>()) {
     if (in_classes) {
       dg = delta;
-    } else {
+    } else if (by_classes) {
       poly_tables<P>(ringb);
       delta_to_classes<P>(delta, dg, sm, ringb);
     }
@@ -1431,8 +1607,12 @@ __device__ int process_quartic(const uint8_t *__restrict__ f35, int max_h, Smem 
   uint8_t *g = gs, *g2 = gn;
   for (int h = 2; h <= max_h; ++h) {
     bool nonzero;
-    if constexpr (theta_by_classes<P>()) nonzero = theta_poly<P>(dg, g, g2, ringb);
-    else nonzero = theta_gather<P>(dg, sm, g, g2, ring);
+    if constexpr (theta_by_classes<P>()) {
+      if (by_classes) nonzero = theta_poly<P>(dg, g, g2, ringb);
+      else nonzero = theta_stream<P>(delta, sm, g, g2, ring);
+    } else {
+      nonzero = theta_gather<P>(dg, sm, g, g2, ring);
+    }
     theta_steps = h - 1;
     if (DEBUG)
       for (int i = tid; i < Pr::ld; i += blockDim.x) dbg.iters[(size_t)(h - 2) * Pr::ld + i] = g2[i];

@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(kThreads, 2) stage_theta(StagedChunk c, const 
   for (unsigned slot = blockIdx.x; slot < total; slot += gridDim.x) {
     if (!c.active[slot]) continue;
     for (int i = threadIdx.x; i < Pr::ld; i += blockDim.x) gs[i] = gin[(size_t)slot * Pr::ld + i];
-    if constexpr (theta_by_classes<P>()) {
+    if constexpr (theta_streams<P>()) {
+      __syncthreads();
+      theta_stream<P>(c.G + slot * gwords, *sm, gs, gn, ring);
+    } else if constexpr (theta_by_classes<P>()) {
       unsigned char *ringb = reinterpret_cast<unsigned char *>(ring);
       poly_tables<P>(ringb);
       delta_to_classes<P>(c.G + slot * gwords, dg, *sm, ringb);
