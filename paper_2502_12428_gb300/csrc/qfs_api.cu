@@ -335,7 +335,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
   int ring_words = 0;
   for (int i = 0; i < prm.n_groups; ++i)
     ring_words = std::max(ring_words, ring_words_for(prm.g[i].p, tile_for(prm.g[i].p),
-                                                     uses_ring_chain(form, prm.g[i].p)));
+                                                     uses_ring_chain(form, prm.g[i].p), power));
   const size_t smem = ring_offset_for(tet(4 * (max_p - 1) + 1)) + 4 * (size_t)ring_words;
   Plan plan;
   rc = make_plan(*S, form, max_p, n_items, opts, plan, smem);
@@ -679,12 +679,11 @@ extern "C" int qfs_poly_power(int d, const uint32_t *coeffs, int n, uint32_t *ou
   if (d < 1 || n < 1 || d * n > 255) return QFS_ERR_INVALID_N;
   if (!coeffs || !out) return QFS_ERR_NULL;
   const int n_in = tet(d + 1);
-  double sum = 0;
+  uint64_t sum = 0;
   for (int i = 0; i < n_in; ++i) sum += coeffs[i];
-  // every output coefficient is at most (sum of the coefficients)^n
-  const double log2_bound = sum <= 1.0 ? 1.0 : n * std::log2(sum);
-  if (log2_bound >= 32.0 * kPolyPowLimbs - 1) return QFS_ERR_INVALID_N;
-  const int nprimes = polypow_primes(log2_bound);
+  // every output coefficient is at most (sum of the coefficients)^n, checked exactly against the output width and
+  // the primes' product
+  const int nprimes = polypow_primes(sum, n);
   if (nprimes == 0) return QFS_ERR_INVALID_N;
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceState *S = nullptr;

@@ -85,7 +85,7 @@ __host__ __device__ inline int chain_slot_words(int p, TileConfig tc) {
   return best;
 }
 
-__host__ __device__ inline int theta_ring_words_for(int p);
+__host__ __device__ inline int theta_ring_words_for(int p, int power = -1);
 
 // Ring words the identity and reduced power modes need: three byte arrays (f^(p-2), Delta_1(f), E), and in the
 // reduced mode a product to degree 4p whose own slot ring (int8 tensor form only) starts after f^(p-2),
@@ -107,9 +107,11 @@ __host__ __device__ inline int aux_ring_words(int p, TileConfig tc, bool ring_ch
 __host__ __device__ constexpr bool uses_ring_chain(int form, int p) { return form == 2 && p > 0; }
 
 // Shared-memory ring words for prime p: the chain's slice ring (when the chain stages slices in shared memory),
-// theta's Delta slots, and the power modes' arrays.  ring_chain = true gives the size every form fits in.
-__host__ __device__ inline int ring_words_for(int p, TileConfig tc, bool ring_chain = true) {
-  return max(max(ring_chain ? chain_slot_words(p, tc) : 0, theta_ring_words_for(p)), aux_ring_words(p, tc, ring_chain));
+// theta's Delta slots, and the power modes' arrays.  ring_chain = true gives the size every form fits in;
+// power (QFS_POWER_*, -1 for every mode) sizes theta for one power mode.
+__host__ __device__ inline int ring_words_for(int p, TileConfig tc, bool ring_chain = true, int power = -1) {
+  return max(max(ring_chain ? chain_slot_words(p, tc) : 0, theta_ring_words_for(p, power)),
+             aux_ring_words(p, tc, ring_chain));
 }
 
 __host__ __device__ inline size_t smem_bytes_for(int p, TileConfig tc, bool ring_chain = true) {
@@ -593,24 +595,30 @@ inline size_t theta_class_words(int p) {
   return b / 4;
 }
 
+// Ring words of theta for one power mode (-1: every mode).  At p = 7 the chain mode streams (theta_stream) and
+// the identity mode runs by classes; the reduced mode keeps its arrays in the power modes' part of the ring.
 template <int P>
-__host__ __device__ constexpr int theta_ring_words() {
+__host__ __device__ constexpr int theta_ring_words(int power = -1) {
   if constexpr (theta_by_classes<P>()) {
     constexpr int poly = (Poly<P>::bytes + 3) / 4;
-    if constexpr (theta_streams<P>()) return poly > theta_stream_ring_words<P>() ? poly : theta_stream_ring_words<P>();
-    else return poly;
+    if constexpr (theta_streams<P>()) {
+      constexpr int stream = theta_stream_ring_words<P>();
+      return power == 0 ? stream : power == 1 ? poly : power == 2 ? 0 : (poly > stream ? poly : stream);
+    } else {
+      return power == 2 ? 0 : poly;
+    }
   } else {
     return (theta_r_words<P>() + 4 * (P - 1) + 2 + 3) & ~3;   // reversed g columns and their slice table
   }
 }
 
-__host__ __device__ inline int theta_ring_words_for(int p) {
+__host__ __device__ inline int theta_ring_words_for(int p, int power) {
   switch (p) {
-    case 3: return theta_ring_words<3>();
-    case 5: return theta_ring_words<5>();
-    case 7: return theta_ring_words<7>();
-    case 11: return theta_ring_words<11>();
-    default: return theta_ring_words<13>();
+    case 3: return theta_ring_words<3>(power);
+    case 5: return theta_ring_words<5>(power);
+    case 7: return theta_ring_words<7>(power);
+    case 11: return theta_ring_words<11>(power);
+    default: return theta_ring_words<13>(power);
   }
 }
 
@@ -998,17 +1006,18 @@ __device__ __forceinline__ void poly_macs(const uint8_t *cube, const uint8_t *tp
 
 // One theta step by residue classes (p <= 7): g (shared, packed) -> gn.  `dc` holds Delta in class order
 // (delta_to_classes) and poly_tables has run.  Class data streams from `dc` into a ring of kPolyStages shared-memory
-// slots by 16-byte cp.async, kPolyStages - 1 classes ahead; each thread then scatters the chunks it copied itself
-// into the cube that the class is multiplied from, so a copy needs no barrier, and one barrier per class separates
-// a cube's scatter from its products.  Two cubes alternate.  Cube positions outside B_d are zero from the start;
-// when the degree d - k of the classes drops, the cube's slab of the old degree is cleared, so each cube always
-// holds zeros outside its current class's cone.  Returns whether some output is nonzero (same value in every
-// thread).
+// slots by 16-byte cp.async, kPolyStages - 1 classes ahead.  Iteration j multiplies class j from one cube while
+// every thread scatters four-byte words of class j + 1 (staged, and complete since the last barrier) into the other
+// cube, then waits for its own copies of class j + 2; one barrier per class.  Cube positions outside B_d are zero
+// from the start; when the degree d - k of the classes drops, the cube's slab of the old degree is cleared, so each
+// cube always holds zeros outside its current class's cone.  Returns whether some output is nonzero (same value in
+// every thread).
 template <int P>
 __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const uint8_t *__restrict__ g,
                                         uint8_t *__restrict__ gn, unsigned char *ring) {
   using Q = Poly<P>;
   constexpr int d = Q::d, ld = Q::ld, C = Q::C, NOUT = Q::NOUT, NS = kPolyStages;
+  static_assert(NS >= 3, "the scatter of class j + 1 and the copies of classes j + 2 .. overlap");
   constexpr int SB = (ld + 15) & ~15;   // bytes of a staging slot (the largest class)
   const int tid = threadIdx.x, nthreads = blockDim.x;
   uint8_t *cube0 = ring;
@@ -1020,7 +1029,7 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
   // taps of every class in class order, and both cubes cleared
   for (int i = tid; i < ld; i += nthreads) taps[i] = g[tapsrc[i]];
   for (int i = tid; i < 2 * Q::CB / 16; i += nthreads) reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
-  // class j -> slot j % NS: this thread copies chunks tid, tid + nthreads, .. of it
+  // class j -> slot j % NS by 16-byte chunks
   auto stage = [&](int j) {
     if (j < Q::NCLS) {
       const int4 c = cls[j];
@@ -1030,21 +1039,21 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
     }
     cp_async_commit();
   };
-  // scatter this thread's chunks of class j (staged) into `cube`
+  // scatter class j (staged and visible to every thread) into `cube`, four bytes per thread at a time
   auto scatter = [&](int j, uint8_t *cube) {
-    const int4 c = cls[j];
-    const int len = tet(d - (c.z & 255) + 1);
-    const uint8_t *src = stg + (j % NS) * SB;
-    for (int i = tid; 16 * i < len; i += nthreads) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(src + 16 * i);
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const int len = tet(d - (cls[j].z & 255) + 1);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(stg + (j % NS) * SB);
+    for (int w = tid; 4 * w < len; w += nthreads) {
+      const uint32_t x = src[w];
 #pragma unroll
-      for (int b = 0; b < 16; ++b)
-        if (16 * i + b < len) cube[cubeaddr[16 * i + b]] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
+      for (int b = 0; b < 4; ++b)
+        if (4 * w + b < len) cube[cubeaddr[4 * w + b]] = (uint8_t)(x >> (8 * b));
     }
   };
   for (int j = 0; j < NS - 1; ++j) stage(j);
-  __syncthreads();   // cubes cleared and taps written
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 3));   // this thread's copies of classes 0 and 1
+  __syncthreads();   // cubes cleared, taps written, classes 0 and 1 staged
+  scatter(0, cube0);
   // output addresses: r_o = tid + kThreads o; threads past B_d read the cube around output (0, 0, 0), and drop it
   int a[NOUT], acc[NOUT];
 #pragma unroll
@@ -1053,14 +1062,12 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
     a[o] = r < ld ? (int)cubeaddr[r] : Q::pad * (C * C + C + 1);
     acc[o] = 0;
   }
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));   // class 0 is staged
-  scatter(0, cube0);
   int degb[2] = {d, d};   // degree of the cone each cube was last filled with (uniform)
   __syncthreads();
   for (int j = 0; j < Q::NCLS; ++j) {
     const int4 c = cls[j];
     const int k = c.z & 255;
-    stage(j + NS - 1);   // into the slot class j - 1 left (scattered by this thread two classes ago)
+    stage(j + NS - 1);   // into the slot of class j - 1, scattered two iterations ago
     const uint8_t *tp = taps + c.y;
     const uint8_t *cube = cube0 + (j & 1) * Q::CB;
     switch (k) {
@@ -1078,9 +1085,9 @@ __device__ __noinline__ bool theta_poly(const uint32_t *__restrict__ dc, const u
         for (int i = tet(nd + 1) + tid; i < tet(degb[b] + 1); i += nthreads) next[cubeaddr[i]] = 0;
         degb[b] = nd;
       }
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2));   // class j + 1 is staged
       scatter(j + 1, next);
     }
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 3));   // this thread's copies of class j + 2
     __syncthreads();
   }
   cp_async_wait_all();

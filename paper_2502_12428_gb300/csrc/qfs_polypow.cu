@@ -289,11 +289,39 @@ uint64_t barrett_mu(uint32_t q) { return (uint64_t)(((unsigned __int128)1 << 64)
 
 }  // namespace
 
-int polypow_primes(double log2_bound) {
-  double acc = 0;
+// Big unsigned integers on the host as little-endian 64-bit limbs, for exact bounds (kBigLimbs x 64 bits).
+namespace {
+constexpr int kBigLimbs = 6;
+// x *= v; returns false if the product does not fit
+bool big_mul(uint64_t (&x)[kBigLimbs], uint64_t v) {
+  unsigned __int128 carry = 0;
+  for (int l = 0; l < kBigLimbs; ++l) {
+    const unsigned __int128 y = (unsigned __int128)x[l] * v + carry;
+    x[l] = (uint64_t)y;
+    carry = y >> 64;
+  }
+  return carry == 0;
+}
+// a > b
+bool big_gt(const uint64_t (&a)[kBigLimbs], const uint64_t (&b)[kBigLimbs]) {
+  for (int l = kBigLimbs - 1; l >= 0; --l)
+    if (a[l] != b[l]) return a[l] > b[l];
+  return false;
+}
+}  // namespace
+
+int polypow_primes(uint64_t sum, int n) {
+  // every coefficient of f^n is at most sum^n; the output holds 32 kPolyPowLimbs bits, and the product of the
+  // primes (largest first) must exceed the bound for the Chinese remaindering to be exact
+  uint64_t bound[kBigLimbs] = {1, 0, 0, 0, 0, 0};
+  for (int i = 0; i < n; ++i)
+    if (!big_mul(bound, sum < 1 ? 1 : sum)) return 0;
+  for (int l = 32 * kPolyPowLimbs / 64; l < kBigLimbs; ++l)
+    if (bound[l]) return 0;
+  uint64_t prod[kBigLimbs] = {1, 0, 0, 0, 0, 0};
   for (int j = 0; j < kPolyPowMaxPrimes; ++j) {
-    acc += 30.0;   // every prime exceeds 2^30
-    if (acc > log2_bound + 1.0) return j + 1;
+    big_mul(prod, kQ[j]);   // at most 7 x 31 bits: fits
+    if (big_gt(prod, bound)) return j + 1;
   }
   return 0;
 }

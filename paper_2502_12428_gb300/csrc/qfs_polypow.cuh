@@ -9,8 +9,9 @@ namespace qfs {
 constexpr int kPolyPowMaxPrimes = 7;   // word-size NTT primes available (their product exceeds 2^215)
 constexpr int kPolyPowLimbs = 8;       // 256-bit output coefficients
 
-// primes needed for coefficients below 2^log2_bound (0 if more than kPolyPowMaxPrimes)
-int polypow_primes(double log2_bound);
+// primes needed to reconstruct coefficients up to sum^n exactly (sum = the sum of the input coefficients); 0 if
+// sum^n does not fit the 256-bit output or needs more than kPolyPowMaxPrimes primes
+int polypow_primes(uint64_t sum, int n);
 // scratch words for powering a degree-d form to the n-th power with nprimes primes (d n <= 255)
 size_t polypow_scratch_words(int d, int n, int nprimes);
 // out: C(d n + 3, 3) x kPolyPowLimbs words; coeffs_dev: C(d + 3, 3) words in device memory
