@@ -52,7 +52,19 @@ __device__ __forceinline__ uint32_t powmod(uint32_t a, uint32_t e, uint32_t q, u
 struct PrimeQ {
   uint32_t q;
   uint64_t mu;
+  uint32_t qneg;   // -q^-1 mod 2^32 (Montgomery reduction)
+  uint32_t rmod;   // 2^32 mod q: 1 in Montgomery form
+  uint32_t r2;     // 2^64 mod q: converts into Montgomery form
 };
+
+// Montgomery product a b 2^-32 mod q for a, b < q < 2^31 (Montgomery's REDC): t + m q is divisible by 2^32 with
+// m = t (-q^-1) mod 2^32, and (t + m q) / 2^32 < 2q
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const PrimeQ &P) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t m = (uint32_t)t * P.qneg;
+  const uint32_t u = (uint32_t)((t + (uint64_t)m * P.q) >> 32);
+  return u >= P.q ? u - P.q : u;
+}
 
 // a = 0, then the packed input reduced mod q
 __global__ void zero_kernel(uint32_t *a, uint32_t N) {
@@ -89,19 +101,45 @@ constexpr int kPassR = 1 << kPassMaxStages;   // longest column of a pass
 constexpr int kPassCols = 32;                 // columns per block in the column passes
 constexpr int kTileWords = kPassR * (kPassCols + 1);
 
-__device__ __forceinline__ uint32_t twiddle_apply(uint32_t x, uint32_t e, const TwTab &T, uint32_t q) {
-  const uint32_t lo = e & ((1u << kTwLoBits) - 1), hi = e >> kTwLoBits;
-  x = shoup_mul(x, __ldg(T.lo + lo), __ldg(T.los + lo), q);
-  return shoup_mul(x, __ldg(T.hi + hi), __ldg(T.his + hi), q);
+// w^e in Montgomery form from the two-level tables (lo and hi hold Montgomery forms)
+__device__ __forceinline__ uint32_t twiddle_mont(uint32_t e, const TwTab &T, const PrimeQ &P) {
+  return mont_mul(__ldg(T.lo + (e & ((1u << kTwLoBits) - 1))), __ldg(T.hi + (e >> kTwLoBits)), P);
 }
 
-// table[j] = base^(j * step), comp[j] = floor(table[j] 2^32 / q), for j < n
+// The twiddles of a column pass's 32 columns in shared memory: for column cc with b = w_M^(c0 + cc),
+// p1[cc][j] = b^j and p2[cc][j] = b^(16 j) (j < 16, Montgomery form), so that b^k = p1[k mod 16] p2[k / 16] for
+// every frequency k < 256 of the column's R-point transform.  Threads 0 .. 63 build them; the caller synchronises.
+__device__ __forceinline__ void column_twiddles(uint32_t (*p1)[16], uint32_t (*p2)[16], uint32_t c0, int lgs,
+                                                const TwTab &T, const PrimeQ &P) {
+  const int t = threadIdx.x;
+  if (t < 2 * kPassCols) {
+    const int cc = t & (kPassCols - 1);
+    uint32_t b = twiddle_mont((c0 + cc) << lgs, T, P);   // w^((c0 + cc) N / M) = w_M^(c0 + cc)
+    uint32_t (*dst)[16] = t < kPassCols ? p1 : p2;
+    if (t >= kPassCols)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) b = mont_mul(b, b, P);   // b^16
+    uint32_t v = P.rmod;
+    for (int j = 0; j < 16; ++j) {
+      dst[cc][j] = v;
+      v = mont_mul(v, b, P);
+    }
+  }
+}
+
+// table[j] = base^(j * step), for j < n: with MONT in Montgomery form (times 2^32 mod q), otherwise with
+// comp[j] = floor(table[j] 2^32 / q) for Shoup's method
+template <bool MONT>
 __global__ void power_table_kernel(uint32_t *table, uint32_t *comp, uint32_t n, uint32_t base, uint32_t step,
                                    PrimeQ P) {
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const uint32_t v = powmod(powmod(base, step, P.q, P.mu), j, P.q, P.mu);
-    table[j] = v;
-    comp[j] = (uint32_t)(((uint64_t)v << 32) / P.q);
+    if (MONT) {
+      table[j] = mulmod(v, P.rmod, P.q, P.mu);
+    } else {
+      table[j] = v;
+      comp[j] = (uint32_t)(((uint64_t)v << 32) / P.q);
+    }
   }
 }
 
@@ -159,6 +197,7 @@ __global__ void __launch_bounds__(256) ntt_column_pass(uint32_t *a, int logN, in
                                                        TwTab TR, PrimeQ P) {
   __shared__ uint32_t tile[kTileWords];
   __shared__ uint32_t rt[kPassR / 2], rts[kPassR / 2];
+  __shared__ uint32_t p1[kPassCols][16], p2[kPassCols][16];
   const int R = 1 << kp, logNc = logM - kp;
   const uint32_t Nc = 1u << logNc, M = 1u << logM;
   const uint32_t q0 = blockIdx.x * kPassCols;            // first column of this block
@@ -166,13 +205,15 @@ __global__ void __launch_bounds__(256) ntt_column_pass(uint32_t *a, int logN, in
   const size_t base = (size_t)bb * M + c0;
   constexpr int ld = kPassCols + 1;
   load_root_table(rt, rts, TR, R, logN);
+  column_twiddles(p1, p2, c0, logN - logM, T, P);
+  if (INV) __syncthreads();
   for (int i = threadIdx.x; i < R * kPassCols; i += blockDim.x) {
     const int m = i / kPassCols, cc = i % kPassCols;
     uint32_t x = a[base + cc + (size_t)m * Nc];
     if (INV) {
+      // the inverse twiddle w_M^(-(c0 + cc) k) (T holds the inverse root's powers)
       const uint32_t k = bitrev(m, kp);
-      const uint32_t e = (uint32_t)(((uint64_t)(c0 + cc) * k) & (M - 1)) << (logN - logM);
-      if (e) x = twiddle_apply(x, e, T, P.q);
+      x = mont_mul(mont_mul(x, p1[cc][k & 15], P), p2[cc][k >> 4], P);
     }
     tile[m * ld + cc] = x;
   }
@@ -185,9 +226,8 @@ __global__ void __launch_bounds__(256) ntt_column_pass(uint32_t *a, int logN, in
     const int m = i / kPassCols, cc = i % kPassCols;
     uint32_t x = tile[m * ld + cc];
     if (!INV) {
-      const uint32_t k = bitrev(m, kp);
-      const uint32_t e = (uint32_t)(((uint64_t)(c0 + cc) * k) & (M - 1)) << (logN - logM);
-      if (e) x = twiddle_apply(x, e, T, P.q);
+      const uint32_t k = bitrev(m, kp);   // the frequency this position holds: times w_M^((c0 + cc) k)
+      x = mont_mul(mont_mul(x, p1[cc][k & 15], P), p2[cc][k >> 4], P);
     }
     a[base + cc + (size_t)m * Nc] = x;
   }
@@ -215,7 +255,14 @@ __global__ void __launch_bounds__(256) ntt_inner_pow(uint32_t *a, int logN, int 
   tile_dif(tile, ld, lgg, kp, rf, rfs, P.q);
   for (int i = threadIdx.x; i < words; i += blockDim.x) {
     const int g = i >> kp, m = i & (R - 1);
-    tile[m * ld + g] = powmod(tile[m * ld + g], n, P.q, P.mu);
+    // x^n by squaring and multiplying in Montgomery form
+    const uint32_t xm = mont_mul(tile[m * ld + g], P.r2, P);
+    uint32_t y = P.rmod, sq = xm;
+    for (uint32_t e = n; e; e >>= 1) {
+      if (e & 1u) y = mont_mul(y, sq, P);
+      sq = mont_mul(sq, sq, P);
+    }
+    tile[m * ld + g] = mont_mul(y, 1u, P);
   }
   __syncthreads();
   tile_dit(tile, ld, lgg, kp, ri, ris, P.q);
@@ -349,11 +396,11 @@ TwTab make_tables(uint32_t *tab, uint32_t w, uint32_t N, PrimeQ P, cudaStream_t 
   const uint32_t R = N < (uint32_t)kPassR ? N : (uint32_t)kPassR;
   const uint32_t nhi = N >> kTwLoBits ? N >> kTwLoBits : 1;
   const uint32_t nlo = N < 4096u ? N : 4096u;
-  power_table_kernel<<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.lo), const_cast<uint32_t *>(T.los), nlo, w, 1, P);
-  power_table_kernel<<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.hi), const_cast<uint32_t *>(T.his), nhi, w, 4096, P);
+  power_table_kernel<true><<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.lo), nullptr, nlo, w, 1, P);
+  power_table_kernel<true><<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.hi), nullptr, nhi, w, 4096, P);
   // w_R^j for j < R / 2, stored at stride kPassR / R so that the R-point roots of every pass are rt[j * (kPassR / R)]
-  power_table_kernel<<<1, 128, 0, st>>>(const_cast<uint32_t *>(T.rt), const_cast<uint32_t *>(T.rts), R / 2, w,
-                                        N / R, P);
+  power_table_kernel<false><<<1, 128, 0, st>>>(const_cast<uint32_t *>(T.rt), const_cast<uint32_t *>(T.rts), R / 2, w,
+                                               N / R, P);
   return T;
 }
 
@@ -382,7 +429,10 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
   C.nprimes = nprimes;
   for (int j = 0; j < nprimes; ++j) {
     const uint32_t q = kQ[j];
-    PrimeQ P{q, barrett_mu(q)};
+    uint32_t qinv = 1;   // q^-1 mod 2^32 by Newton's iteration (each step doubles the correct low bits)
+    for (int i = 0; i < 5; ++i) qinv *= 2u - q * qinv;
+    const uint32_t rmod = (uint32_t)((((uint64_t)1) << 32) % q);
+    PrimeQ P{q, barrett_mu(q), 0u - qinv, rmod, (uint32_t)host_mulmod(rmod, rmod, q)};
     C.q[j] = q;
     C.mu[j] = P.mu;
     for (int k = 0; k < kPolyPowMaxPrimes; ++k) C.inv[j][k] = k < j ? (uint32_t)host_powmod(kQ[k] % q, q - 2, q) : 0u;
