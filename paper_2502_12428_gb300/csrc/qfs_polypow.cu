@@ -146,31 +146,71 @@ __global__ void power_table_kernel(uint32_t *table, uint32_t *comp, uint32_t n, 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
 
 // R-point DIF (natural in, bit-reversed out) on the columns of a shared tile: element m of column cc at
-// tile[m * ld + cc], 2^lgcol columns, R = 2^kp; twiddles w_R^j from rt (stage of length len uses w_R^(j R / len)).
-// Index arithmetic by shifts and masks (every extent is a power of two).
+// tile[m * ld + cc], 2^lgcol columns, R = 2^kp; twiddles w_R^j from rt (a stage of length len uses w_R^(j R / len)).
+// Stages run two at a time (radix 4: four elements j, j + L/4, j + L/2, j + 3L/4 of a block of length L through
+// the stages of lengths L and L/2, in registers); an odd stage count starts with one radix-2 stage.  Index
+// arithmetic by shifts and masks (every extent is a power of two).
 __device__ __forceinline__ void tile_dif(uint32_t *tile, int ld, int lgcol, int kp, const uint32_t *rt,
                                          const uint32_t *rts, uint32_t q) {
-  const int R = 1 << kp, nb = 1 << (lgcol + kp - 1);
-  for (int lglen = kp; lglen >= 1; --lglen) {
+  const int cmask = (1 << lgcol) - 1;
+  int lglen = kp;
+  if (kp & 1) {
     const int h = 1 << (lglen - 1), lgts = kp - lglen;
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-      const int cc = t & ((1 << lgcol) - 1), b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+    for (int t = threadIdx.x; t < (1 << (lgcol + kp - 1)); t += blockDim.x) {
+      const int cc = t & cmask, b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
       const uint32_t u = tile[i0 * ld + cc], v = tile[i1 * ld + cc];
       tile[i0 * ld + cc] = addmod(u, v, q);
       tile[i1 * ld + cc] = shoup_mul(submod(u, v, q), rt[j << lgts], rts[j << lgts], q);
     }
     __syncthreads();
+    --lglen;
   }
-  (void)R;
+  for (; lglen >= 2; lglen -= 2) {
+    const int L4 = 1 << (lglen - 2), lgts = kp - lglen;
+    for (int t = threadIdx.x; t < (1 << (lgcol + kp - 2)); t += blockDim.x) {
+      const int cc = t & cmask, u = t >> lgcol, j = u & (L4 - 1), base = ((u - j) << 2) + j;
+      uint32_t *x0 = tile + base * ld + cc, *x1 = x0 + L4 * ld, *x2 = x1 + L4 * ld, *x3 = x2 + L4 * ld;
+      const uint32_t a0 = *x0, a1 = *x1, a2 = *x2, a3 = *x3;
+      const int k1 = j << lgts, k2 = (j + L4) << lgts, k3 = j << (lgts + 1);
+      const uint32_t b0 = addmod(a0, a2, q), b2 = shoup_mul(submod(a0, a2, q), rt[k1], rts[k1], q);
+      const uint32_t b1 = addmod(a1, a3, q), b3 = shoup_mul(submod(a1, a3, q), rt[k2], rts[k2], q);
+      *x0 = addmod(b0, b1, q);
+      *x1 = shoup_mul(submod(b0, b1, q), rt[k3], rts[k3], q);
+      *x2 = addmod(b2, b3, q);
+      *x3 = shoup_mul(submod(b2, b3, q), rt[k3], rts[k3], q);
+    }
+    __syncthreads();
+  }
 }
-// R-point inverse DIT (bit-reversed in, natural out), twiddles w_R^-j
+// R-point inverse DIT (bit-reversed in, natural out), twiddles w_R^-j: stages of lengths 2, 4, .., R, two at a time
+// (lengths L/2 and L on the four elements j, j + L/4, j + L/2, j + 3L/4), an odd count ending with one radix-2 stage
 __device__ __forceinline__ void tile_dit(uint32_t *tile, int ld, int lgcol, int kp, const uint32_t *rt,
                                          const uint32_t *rts, uint32_t q) {
-  const int nb = 1 << (lgcol + kp - 1);
-  for (int lglen = 1; lglen <= kp; ++lglen) {
+  const int cmask = (1 << lgcol) - 1;
+  int lglen = 2;
+  for (; lglen <= kp; lglen += 2) {
+    const int L4 = 1 << (lglen - 2), lgts = kp - lglen;
+    for (int t = threadIdx.x; t < (1 << (lgcol + kp - 2)); t += blockDim.x) {
+      const int cc = t & cmask, u = t >> lgcol, j = u & (L4 - 1), base = ((u - j) << 2) + j;
+      uint32_t *x0 = tile + base * ld + cc, *x1 = x0 + L4 * ld, *x2 = x1 + L4 * ld, *x3 = x2 + L4 * ld;
+      const int k1 = j << lgts, k2 = (j + L4) << lgts, k3 = j << (lgts + 1);
+      const uint32_t a0 = *x0, a1 = shoup_mul(*x1, rt[k3], rts[k3], q);
+      const uint32_t a2 = *x2, a3 = shoup_mul(*x3, rt[k3], rts[k3], q);
+      const uint32_t u0 = addmod(a0, a1, q), u1 = submod(a0, a1, q);
+      const uint32_t u2 = shoup_mul(addmod(a2, a3, q), rt[k1], rts[k1], q);
+      const uint32_t u3 = shoup_mul(submod(a2, a3, q), rt[k2], rts[k2], q);
+      *x0 = addmod(u0, u2, q);
+      *x2 = submod(u0, u2, q);
+      *x1 = addmod(u1, u3, q);
+      *x3 = submod(u1, u3, q);
+    }
+    __syncthreads();
+  }
+  if (kp & 1) {
+    lglen = kp;
     const int h = 1 << (lglen - 1), lgts = kp - lglen;
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-      const int cc = t & ((1 << lgcol) - 1), b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
+    for (int t = threadIdx.x; t < (1 << (lgcol + kp - 1)); t += blockDim.x) {
+      const int cc = t & cmask, b = t >> lgcol, j = b & (h - 1), i0 = ((b - j) << 1) + j, i1 = i0 + h;
       const uint32_t u = tile[i0 * ld + cc], v = shoup_mul(tile[i1 * ld + cc], rt[j << lgts], rts[j << lgts], q);
       tile[i0 * ld + cc] = addmod(u, v, q);
       tile[i1 * ld + cc] = submod(u, v, q);
