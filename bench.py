@@ -49,6 +49,18 @@ LANES = {"int32": 64, "dp4a": 64 * 4, "int8tc": 64 * 4}
 PEAK_KIND = {"int32": "imad", "dp4a": "dp4a", "int8tc": "mma_s8"}
 CPU_SAMPLE_A = 1024     # route-A quartics of the CPU baseline (about half a minute on 16 cores at p = 7)
 
+def hbm_peak():
+    """The measured HBM copy rate of this machine's GB300 (MEASURED_PEAKS.json, driver-written), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return {"gbs": float(json.load(fh)["hbm_gbs"]), "basis": "measured copy rate (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"gbs": 6800.0, "basis": "fallback 6.8 TB/s (no measured copy rate present)"}
+
+
+HBM_PEAK = hbm_peak()
+
 
 # ----------------------------------------------------------------------------------------------- work counts
 def n_mon(d):
@@ -536,8 +548,17 @@ def run_ours(args):
             qfs.poly_power_limbs(16, f16, npow, out=limbs)
             e1.record(stream)
             torch.cuda.synchronize()
-            extra[f"poly-power-deg16-n{npow}"] = {"seconds": round(mx(e0.elapsed_time(e1)) / 1e3, 5),
-                                                 "unit": "s per power", "output_terms": n_out}
+            sec = mx(e0.elapsed_time(e1)) / 1e3
+            plan = qfs.poly_power_info(16, f16, npow)
+            gbs = plan["hbm_bytes"] / sec / 1e9
+            extra[f"poly-power-deg16-n{npow}"] = {
+                "seconds": round(sec, 5), "unit": "s per power", "output_terms": n_out, "primes": plan["nprimes"],
+                "transform_len": plan["transform_len"],
+                "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "unit": "GB/s",
+                             "peak": HBM_PEAK["gbs"], "peak_basis": HBM_PEAK["basis"],
+                             "frac": round(gbs / HBM_PEAK["gbs"], 4), "traffic": None,
+                             "bytes_per_call": plan["hbm_bytes"],
+                             "bytes_basis": "qfs_poly_power_info: reads + writes of every kernel as launched"}}
             del limbs
 
     # end to end through the public API: pinned host input -> H2D -> heights -> D2H, every step

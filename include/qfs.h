@@ -227,6 +227,20 @@ int qfs_matmul_mod(int p, int n, int m, int k, const uint8_t *A, const uint8_t *
    QFS_ERR_NULL, QFS_ERR_NO_MEMORY, QFS_ERR_CUDA. */
 int qfs_poly_power(int d, const uint32_t *coeffs, int n, uint32_t *out, cudaStream_t stream);
 
+/* The plan of one qfs_poly_power call, without running it (host only, no GPU work): the number of NTT primes it
+   takes, the transform length N (the power of two >= (d n + 1)^3), and the algorithmic device-memory bytes of the
+   call, which are the reads plus writes of its kernels as launched:
+   - the twiddle tables of every prime;
+   - per prime: clearing and filling the packed input, and one read and one write of the N-word transform buffer
+     per pass (2 k + 1 passes, k = the outer passes of 8 or fewer stages);
+   - the gather of the output residues;
+   - the Chinese remaindering.
+   Any of nprimes, transform_len, hbm_bytes may be NULL.  coeffs: HOST, as for qfs_poly_power.  Returns QFS_OK,
+   QFS_ERR_INVALID_N (the same conditions as qfs_poly_power) or QFS_ERR_NULL (coeffs NULL).  No counterpart in the
+   paper: it states the traffic that the powering's roofline divides by. */
+int qfs_poly_power_info(int d, const uint32_t *coeffs, int n, int *nprimes, uint64_t *transform_len,
+                        uint64_t *hbm_bytes);
+
 #ifdef __cplusplus
 }
 #endif

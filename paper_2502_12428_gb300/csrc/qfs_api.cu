@@ -707,3 +707,16 @@ extern "C" int qfs_poly_power(int d, const uint32_t *coeffs, int n, uint32_t *ou
   e = polypow_launch(d, n, nprimes, cdev, out, scratch, stream);
   return e == cudaSuccess ? QFS_OK : cuda_fail(e);
 }
+
+extern "C" int qfs_poly_power_info(int d, const uint32_t *coeffs, int n, int *nprimes, uint64_t *transform_len,
+                                   uint64_t *hbm_bytes) {
+  if (d < 1 || n < 1 || d * n > 255) return QFS_ERR_INVALID_N;
+  if (!coeffs) return QFS_ERR_NULL;
+  uint64_t sum = 0;
+  for (int i = 0; i < tet(d + 1); ++i) sum += coeffs[i];
+  const int np = polypow_primes(sum, n);
+  if (np == 0) return QFS_ERR_INVALID_N;
+  if (nprimes) *nprimes = np;
+  polypow_plan(d, n, np, transform_len, hbm_bytes);
+  return QFS_OK;
+}

@@ -89,6 +89,33 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t a, uint32_t w, uint32_t w
   return r >= q ? r - q : r;
 }
 
+// One power table of a batch: table[j] = base^(j step) for j < n, in Montgomery form (mont) or with Shoup
+// companions comp[j].
+struct TableJob {
+  uint32_t *table, *comp;
+  uint32_t n, base, step;
+  int mont;
+  PrimeQ P;
+};
+constexpr int kMaxTableJobs = 3 * 2 * kPolyPowMaxPrimes;
+struct TableJobs {
+  TableJob job[kMaxTableJobs];
+};
+// Every power table of every prime and direction in one launch: blockIdx.y selects the table.
+__global__ void power_tables_kernel(TableJobs J) {
+  const TableJob &T = J.job[blockIdx.y];
+  const uint32_t b = powmod(T.base, T.step, T.P.q, T.P.mu);
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < T.n; j += gridDim.x * blockDim.x) {
+    const uint32_t v = powmod(b, j, T.P.q, T.P.mu);
+    if (T.mont) {
+      T.table[j] = mulmod(v, T.P.rmod, T.P.q, T.P.mu);
+    } else {
+      T.table[j] = v;
+      T.comp[j] = (uint32_t)(((uint64_t)v << 32) / T.P.q);
+    }
+  }
+}
+
 // Twiddle tables of one prime and direction: lo[j] = w^j (j < 4096), hi[j] = w^(4096 j) (j < max(1, N / 4096)),
 // each with its Shoup companion, so that w^e = lo[e mod 4096] hi[e / 4096]; rt[j] = w_R^j (j < R / 2) for the
 // R-point transforms inside a pass, R = min(256, N), also with companions.
@@ -123,22 +150,6 @@ __device__ __forceinline__ void column_twiddles(uint32_t (*p1)[16], uint32_t (*p
     for (int j = 0; j < 16; ++j) {
       dst[cc][j] = v;
       v = mont_mul(v, b, P);
-    }
-  }
-}
-
-// table[j] = base^(j * step), for j < n: with MONT in Montgomery form (times 2^32 mod q), otherwise with
-// comp[j] = floor(table[j] 2^32 / q) for Shoup's method
-template <bool MONT>
-__global__ void power_table_kernel(uint32_t *table, uint32_t *comp, uint32_t n, uint32_t base, uint32_t step,
-                                   PrimeQ P) {
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t v = powmod(powmod(base, step, P.q, P.mu), j, P.q, P.mu);
-    if (MONT) {
-      table[j] = mulmod(v, P.rmod, P.q, P.mu);
-    } else {
-      table[j] = v;
-      comp[j] = (uint32_t)(((uint64_t)v << 32) / P.q);
     }
   }
 }
@@ -312,6 +323,242 @@ __global__ void __launch_bounds__(256) ntt_inner_pow(uint32_t *a, int logN, int 
   }
 }
 
+// ------------------------------------------------------------------------------------ register-resident passes
+// A pass of KP <= 8 stages in two register phases with one exchange through shared memory between them.  With
+// K1 = KP / 2 and K2 = KP - K1, the element m of an R-point column (R = 2^KP) is written m = m0 + (k << K2)
+// (m0 < 2^K2, k < 2^K1) or m = (g << K2) + r (g < 2^K1, r < 2^K2).  In the DIF, the stages of lengths R .. 2^(K2+1)
+// pair elements with the same m0 (a 2^K1-point sub-transform per m0, in registers), and the stages of lengths
+// 2^K2 .. 2 stay inside one block g of 2^K2 consecutive elements (a 2^K2-point sub-transform per g).  The inverse
+// DIT takes the same two groups in the opposite order.  Every element is loaded and stored once per pass and goes
+// through shared memory once, against one shared-memory round trip per stage pair in tile_dif / tile_dit.
+constexpr int kNttThreads = 256;
+
+__host__ __device__ constexpr uint32_t bitrev_c(uint32_t x, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+// In-register DIF stages on x[k] = X[m0 + (k << S)], k < 2^K, of an R-point transform (R = 2^KP): the stages of
+// lengths 2^(S+K) .. 2^(S+1).  The stage of half-length h = 2^t in k pairs (k, k + h) for k mod 2h < h, with the
+// twiddle w_R^(j R / len) = rt[j << (KP - S - t - 1)], j = m0 + ((k mod h) << S) (rt[e] = w_R^e, Shoup companions
+// in rts).  M0ZERO: m0 is 0, so the pairs with k mod h = 0 take w^0 and skip the product.
+template <int KP, int K, int S, bool M0ZERO>
+__device__ __forceinline__ void reg_dif(uint32_t (&x)[1 << K], int m0, const uint32_t *rt, const uint32_t *rts,
+                                        uint32_t q) {
+#pragma unroll
+  for (int t = K - 1; t >= 0; --t) {
+    const int h = 1 << t, sh = KP - S - t - 1;
+#pragma unroll
+    for (int k = 0; k < (1 << K); ++k) {
+      if (k & h) continue;
+      const uint32_t u = x[k], v = x[k + h];
+      x[k] = addmod(u, v, q);
+      if (M0ZERO && (k & (h - 1)) == 0) {
+        x[k + h] = submod(u, v, q);
+      } else {
+        const int e = (m0 + ((k & (h - 1)) << S)) << sh;
+        x[k + h] = shoup_mul(submod(u, v, q), rt[e], rts[e], q);
+      }
+    }
+  }
+}
+
+// In-register inverse DIT stages on x[k] = X[m0 + (k << S)]: lengths 2^(S+1) .. 2^(S+K), twiddles as in reg_dif
+// (rt holds the inverse root's powers).
+template <int KP, int K, int S, bool M0ZERO>
+__device__ __forceinline__ void reg_dit(uint32_t (&x)[1 << K], int m0, const uint32_t *rt, const uint32_t *rts,
+                                        uint32_t q) {
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int h = 1 << t, sh = KP - S - t - 1;
+#pragma unroll
+    for (int k = 0; k < (1 << K); ++k) {
+      if (k & h) continue;
+      uint32_t v = x[k + h];
+      if (!(M0ZERO && (k & (h - 1)) == 0)) {
+        const int e = (m0 + ((k & (h - 1)) << S)) << sh;
+        v = shoup_mul(v, rt[e], rts[e], q);
+      }
+      const uint32_t u = x[k];
+      x[k] = addmod(u, v, q);
+      x[k + h] = submod(u, v, q);
+    }
+  }
+}
+
+// Element m of column cc (frequency k = bitrev(m)) times w_M^(+-(c0 + cc) k) from the column's p1 / p2 tables.
+__device__ __forceinline__ uint32_t column_twiddle(uint32_t x, const uint32_t *p1c, const uint32_t *p2c, uint32_t k,
+                                                   const PrimeQ &P) {
+  return mont_mul(mont_mul(x, p1c[k & 15], P), p2c[k >> 4], P);
+}
+
+// A column pass of KP stages (2 <= KP <= 8) with the layout of ntt_column_pass: column q = (block bb, offset c)
+// holds a[bb M + c + m Nc], m < R = 2^KP; each block takes kPassCols consecutive columns.  A task (cc, m0) holds
+// rows m0 + (k << K2) of column cc, a task (cc, g) rows (g << K2) + r; the lanes of a warp are 32 consecutive
+// columns, so every global access is one 128-byte row segment and every shared-memory access is free of conflicts
+// (row stride kPassCols + 1).
+template <int KP, bool INV>
+__global__ void __launch_bounds__(kNttThreads) ntt_column_regs(uint32_t *a, int logN, int logM, TwTab T, TwTab TR,
+                                                               PrimeQ P) {
+  static_assert(KP >= 2 && KP <= kPassMaxStages, "two register phases");
+  constexpr int K1 = KP / 2, K2 = KP - K1, ld = kPassCols + 1;
+  constexpr int NT1 = kPassCols << K2, NT2 = kPassCols << K1;   // tasks of the strided and the contiguous phase
+  __shared__ uint32_t tile[(1 << KP) * ld];
+  __shared__ uint32_t rt[kPassR / 2], rts[kPassR / 2];
+  __shared__ uint32_t p1[kPassCols][16], p2[kPassCols][16];
+  const int logNc = logM - KP;
+  const uint32_t Nc = 1u << logNc;
+  const uint32_t q0 = blockIdx.x * kPassCols;
+  const uint32_t bb = q0 >> logNc, c0 = q0 & (Nc - 1);
+  uint32_t *col = a + ((size_t)bb << logM) + c0;
+  load_root_table(rt, rts, TR, 1 << KP, logN);
+  column_twiddles(p1, p2, c0, logN - logM, T, P);
+  __syncthreads();
+  if (!INV) {
+#pragma unroll
+    for (int it = 0; it < (NT1 + kNttThreads - 1) / kNttThreads; ++it) {
+      const int task = threadIdx.x + it * kNttThreads;
+      if (task < NT1) {
+        const int cc = task & (kPassCols - 1), m0 = task >> 5;
+        uint32_t x[1 << K1];
+#pragma unroll
+        for (int k = 0; k < (1 << K1); ++k) x[k] = col[cc + (size_t)(m0 + (k << K2)) * Nc];
+        reg_dif<KP, K1, K2, false>(x, m0, rt, rts, P.q);
+#pragma unroll
+        for (int k = 0; k < (1 << K1); ++k) tile[(m0 + (k << K2)) * ld + cc] = x[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < (NT2 + kNttThreads - 1) / kNttThreads; ++it) {
+      const int task = threadIdx.x + it * kNttThreads;
+      if (task < NT2) {
+        const int cc = task & (kPassCols - 1), g = task >> 5;
+        uint32_t x[1 << K2];
+#pragma unroll
+        for (int r = 0; r < (1 << K2); ++r) x[r] = tile[((g << K2) + r) * ld + cc];
+        reg_dif<KP, K2, 0, true>(x, 0, rt, rts, P.q);
+        const uint32_t bg = bitrev(g, K1);
+#pragma unroll
+        for (int r = 0; r < (1 << K2); ++r) {
+          // position (g << K2) + r holds frequency bitrev_KP = (bitrev_K2(r) << K1) | bitrev_K1(g)
+          const uint32_t k = (bitrev_c(r, K2) << K1) | bg;
+          col[cc + (size_t)((g << K2) + r) * Nc] = column_twiddle(x[r], p1[cc], p2[cc], k, P);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < (NT2 + kNttThreads - 1) / kNttThreads; ++it) {
+      const int task = threadIdx.x + it * kNttThreads;
+      if (task < NT2) {
+        const int cc = task & (kPassCols - 1), g = task >> 5;
+        const uint32_t bg = bitrev(g, K1);
+        uint32_t x[1 << K2];
+#pragma unroll
+        for (int r = 0; r < (1 << K2); ++r) {
+          // the inverse twiddle w_M^(-(c0 + cc) k) (T holds the inverse root's powers)
+          const uint32_t k = (bitrev_c(r, K2) << K1) | bg;
+          x[r] = column_twiddle(col[cc + (size_t)((g << K2) + r) * Nc], p1[cc], p2[cc], k, P);
+        }
+        reg_dit<KP, K2, 0, true>(x, 0, rt, rts, P.q);
+#pragma unroll
+        for (int r = 0; r < (1 << K2); ++r) tile[((g << K2) + r) * ld + cc] = x[r];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < (NT1 + kNttThreads - 1) / kNttThreads; ++it) {
+      const int task = threadIdx.x + it * kNttThreads;
+      if (task < NT1) {
+        const int cc = task & (kPassCols - 1), m0 = task >> 5;
+        uint32_t x[1 << K1];
+#pragma unroll
+        for (int k = 0; k < (1 << K1); ++k) x[k] = tile[(m0 + (k << K2)) * ld + cc];
+        reg_dit<KP, K1, K2, false>(x, m0, rt, rts, P.q);
+#pragma unroll
+        for (int k = 0; k < (1 << K1); ++k) col[cc + (size_t)(m0 + (k << K2)) * Nc] = x[k];
+      }
+    }
+  }
+}
+
+// x^n for x < q (normal form) by Montgomery products on normal-form operands: every product carries a factor
+// 2^-32, so the square-and-multiply chain gives x^n 2^(-32(n-1)), and one product with c = 2^(32 n) mod q restores
+// x^n.  n >= 1.
+__device__ __forceinline__ uint32_t pow_mont(uint32_t x, uint32_t n, uint32_t c, const PrimeQ &P) {
+  uint32_t sq = x, e = n;
+  while (!(e & 1u)) {
+    sq = mont_mul(sq, sq, P);
+    e >>= 1;
+  }
+  uint32_t y = sq;
+  for (e >>= 1; e; e >>= 1) {
+    sq = mont_mul(sq, sq, P);
+    if (e & 1u) y = mont_mul(y, sq, P);
+  }
+  return mont_mul(y, c, P);
+}
+
+// The innermost pass for N >= kPassR kPassCols: a block takes kPassCols runs of R = kPassR contiguous elements
+// (element m of run g at a[blk + g R + m]).  Strided phase of the forward DIF (task (g, m0)), then per block of 2^K2
+// consecutive elements (task (g, b)) the contiguous phase, the n-th powers and the contiguous phase of the inverse
+// DIT without leaving registers, then the strided phase of the inverse.  Shared tile: run g, element m at
+// g RW + (m >> K2) BW + (m mod 2^K2) with blocks padded to BW = 2^K2 + 1 words, so that both phases' accesses
+// (16 lanes per run, two runs per warp) are free of bank conflicts.  cn = 2^(32 n) mod q (pow_mont).
+__global__ void __launch_bounds__(kNttThreads) ntt_inner_regs(uint32_t *a, int logN, uint32_t n, uint32_t cn,
+                                                              TwTab TF, TwTab TI, PrimeQ P) {
+  constexpr int KP = kPassMaxStages, K1 = KP / 2, K2 = KP - K1, G = kPassCols;
+  constexpr int BW = (1 << K2) + 1, RW = (1 << K1) * BW;
+  constexpr int NT1 = G << K2, NT2 = G << K1;
+  __shared__ uint32_t tile[G * RW];
+  __shared__ uint32_t rf[kPassR / 2], rfs[kPassR / 2], ri[kPassR / 2], ris[kPassR / 2];
+  uint32_t *blk = a + ((size_t)blockIdx.x << (KP + 5));
+  static_assert(G == 32, "32 runs per block");
+  load_root_table(rf, rfs, TF, 1 << KP, logN);
+  load_root_table(ri, ris, TI, 1 << KP, logN);
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < NT1 / kNttThreads; ++it) {
+    const int task = threadIdx.x + it * kNttThreads;
+    const int m0 = task & ((1 << K2) - 1), g = task >> K2;
+    uint32_t x[1 << K1];
+#pragma unroll
+    for (int k = 0; k < (1 << K1); ++k) x[k] = blk[(g << KP) + m0 + (k << K2)];
+    reg_dif<KP, K1, K2, false>(x, m0, rf, rfs, P.q);
+#pragma unroll
+    for (int k = 0; k < (1 << K1); ++k) tile[g * RW + k * BW + m0] = x[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < NT2 / kNttThreads; ++it) {
+    const int task = threadIdx.x + it * kNttThreads;
+    const int b = task & ((1 << K1) - 1), g = task >> K1;
+    uint32_t x[1 << K2];
+#pragma unroll
+    for (int r = 0; r < (1 << K2); ++r) x[r] = tile[g * RW + b * BW + r];
+    reg_dif<KP, K2, 0, true>(x, 0, rf, rfs, P.q);
+#pragma unroll
+    for (int r = 0; r < (1 << K2); ++r) x[r] = pow_mont(x[r], n, cn, P);
+    reg_dit<KP, K2, 0, true>(x, 0, ri, ris, P.q);
+#pragma unroll
+    for (int r = 0; r < (1 << K2); ++r) tile[g * RW + b * BW + r] = x[r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < NT1 / kNttThreads; ++it) {
+    const int task = threadIdx.x + it * kNttThreads;
+    const int m0 = task & ((1 << K2) - 1), g = task >> K2;
+    uint32_t x[1 << K1];
+#pragma unroll
+    for (int k = 0; k < (1 << K1); ++k) x[k] = tile[g * RW + k * BW + m0];
+    reg_dit<KP, K1, K2, false>(x, m0, ri, ris, P.q);
+#pragma unroll
+    for (int k = 0; k < (1 << K1); ++k) blk[(g << KP) + m0 + (k << K2)] = x[k];
+  }
+}
+
 // residue of every output coefficient (packed descending lex, degree D = d n), times N^-1
 __global__ void gather_kernel(const uint32_t *a, int D, int B, uint32_t ninv, uint32_t *res, PrimeQ P) {
   const int n_out = tet(D + 1);
@@ -421,13 +668,34 @@ size_t polypow_scratch_words(int d, int n, int nprimes) {
   const int B = d * n + 1;
   uint32_t N = 1;
   while ((uint64_t)N < (uint64_t)B * B * B) N <<= 1;
-  return (size_t)N + 2 * kTwWords + (size_t)nprimes * tet(d * n + 1) + tet(d + 1) + 64;
+  return (size_t)N + 2 * kTwWords * (size_t)nprimes + (size_t)nprimes * tet(d * n + 1) + tet(d + 1) + 64;
+}
+
+void polypow_plan(int d, int n, int nprimes, uint64_t *transform_len, uint64_t *bytes) {
+  const int B = d * n + 1;
+  uint64_t N = 1;
+  int logN = 0;
+  while (N < (uint64_t)B * B * B) { N <<= 1; ++logN; }
+  const int inner = logN < kPassMaxStages ? logN : kPassMaxStages;
+  const int n_outer = (logN - inner + kPassMaxStages - 1) / kPassMaxStages;
+  const uint64_t n_in = tet(d + 1), n_out = tet(d * n + 1);
+  const uint64_t R = N < (uint64_t)kPassR ? N : (uint64_t)kPassR;
+  const uint64_t nlo = N < 4096 ? N : 4096, nhi = N >> kTwLoBits ? N >> kTwLoBits : 1;
+  // per prime and direction: the lo and hi tables (one word each) and the R / 2 roots with their companions
+  const uint64_t tables = 2 * 4 * (nlo + nhi + R);
+  const uint64_t per_prime = tables + 4 * N                  // clear the transform buffer
+                             + 4 * 2 * n_in                   // read the input, write it into the buffer
+                             + (uint64_t)(2 * n_outer + 1) * 8 * N   // every pass reads and writes the buffer
+                             + 8 * n_out;                     // gather: read a residue, write it
+  if (transform_len) *transform_len = N;
+  if (bytes) *bytes = (uint64_t)nprimes * per_prime + n_out * (4ull * nprimes + 4ull * kPolyPowLimbs);
 }
 
 namespace {
 
-// Tables of w (forward) or w^-1 (inverse) for a length-N transform, in tab (kTwWords words).
-TwTab make_tables(uint32_t *tab, uint32_t w, uint32_t N, PrimeQ P, cudaStream_t st) {
+// Tables of w (forward) or w^-1 (inverse) for a length-N transform in tab (kTwWords words): fills the pointers and
+// appends the three table jobs to J (built later by one power_tables_kernel launch).
+TwTab plan_tables(uint32_t *tab, uint32_t w, uint32_t N, const PrimeQ &P, TableJobs &J, int &njobs) {
   TwTab T;
   uint32_t *p = tab;
   T.lo = p; T.los = p + 4096; p += 8192;
@@ -436,12 +704,34 @@ TwTab make_tables(uint32_t *tab, uint32_t w, uint32_t N, PrimeQ P, cudaStream_t 
   const uint32_t R = N < (uint32_t)kPassR ? N : (uint32_t)kPassR;
   const uint32_t nhi = N >> kTwLoBits ? N >> kTwLoBits : 1;
   const uint32_t nlo = N < 4096u ? N : 4096u;
-  power_table_kernel<true><<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.lo), nullptr, nlo, w, 1, P);
-  power_table_kernel<true><<<16, 256, 0, st>>>(const_cast<uint32_t *>(T.hi), nullptr, nhi, w, 4096, P);
-  // w_R^j for j < R / 2, stored at stride kPassR / R so that the R-point roots of every pass are rt[j * (kPassR / R)]
-  power_table_kernel<false><<<1, 128, 0, st>>>(const_cast<uint32_t *>(T.rt), const_cast<uint32_t *>(T.rts), R / 2, w,
-                                               N / R, P);
+  J.job[njobs++] = TableJob{const_cast<uint32_t *>(T.lo), nullptr, nlo, w, 1, 1, P};
+  J.job[njobs++] = TableJob{const_cast<uint32_t *>(T.hi), nullptr, nhi, w, 4096, 1, P};
+  // w_R^j for j < R / 2 with Shoup companions: the R-point roots of every pass are rt[j * (kPassR / R)]
+  J.job[njobs++] = TableJob{const_cast<uint32_t *>(T.rt), const_cast<uint32_t *>(T.rts), R / 2, w, N / R, 0, P};
   return T;
+}
+
+// One column pass of kp stages: the register-phase kernel for kp >= 2, the shared-memory stage loop for kp = 1.
+void column_pass(bool inv, int kp, uint32_t blocks, uint32_t *a, int logN, int logM, const TwTab &T, const PrimeQ &P,
+                 cudaStream_t st) {
+#define QFS_COLUMN_PASS(KP)                                                                               \
+  case KP:                                                                                                \
+    if (inv) ntt_column_regs<KP, true><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P);           \
+    else ntt_column_regs<KP, false><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P);              \
+    break;
+  switch (kp) {
+    QFS_COLUMN_PASS(2)
+    QFS_COLUMN_PASS(3)
+    QFS_COLUMN_PASS(4)
+    QFS_COLUMN_PASS(5)
+    QFS_COLUMN_PASS(6)
+    QFS_COLUMN_PASS(7)
+    QFS_COLUMN_PASS(8)
+    default:
+      if (inv) ntt_column_pass<true><<<blocks, 256, 0, st>>>(a, logN, logM, kp, T, T, P);
+      else ntt_column_pass<false><<<blocks, 256, 0, st>>>(a, logN, logM, kp, T, T, P);
+  }
+#undef QFS_COLUMN_PASS
 }
 
 }  // namespace
@@ -454,8 +744,8 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
   while ((uint64_t)N < (uint64_t)B * B * B) { N <<= 1; ++logN; }
   const int n_out = tet(D + 1);
   uint32_t *a = scratch;
-  uint32_t *twf = a + N, *twi = twf + kTwWords;
-  uint32_t *res = twi + kTwWords;
+  uint32_t *tw = a + N;                               // forward and inverse tables of every prime
+  uint32_t *res = tw + 2 * kTwWords * (size_t)nprimes;
   const int grid = 152 * 8, block = 256;
   // passes: the innermost takes min(8, logN) stages on contiguous runs; the rest, outermost first, up to 8 each
   const int inner = logN < kPassMaxStages ? logN : kPassMaxStages;
@@ -467,35 +757,49 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
   }
   CrtParams C;
   C.nprimes = nprimes;
+  PrimeQ PQ[kPolyPowMaxPrimes];
+  TwTab TF[kPolyPowMaxPrimes], TI[kPolyPowMaxPrimes];
+  uint32_t ninv[kPolyPowMaxPrimes];
+  TableJobs J;
+  int njobs = 0;
   for (int j = 0; j < nprimes; ++j) {
     const uint32_t q = kQ[j];
     uint32_t qinv = 1;   // q^-1 mod 2^32 by Newton's iteration (each step doubles the correct low bits)
     for (int i = 0; i < 5; ++i) qinv *= 2u - q * qinv;
     const uint32_t rmod = (uint32_t)((((uint64_t)1) << 32) % q);
-    PrimeQ P{q, barrett_mu(q), 0u - qinv, rmod, (uint32_t)host_mulmod(rmod, rmod, q)};
+    PQ[j] = PrimeQ{q, barrett_mu(q), 0u - qinv, rmod, (uint32_t)host_mulmod(rmod, rmod, q)};
     C.q[j] = q;
-    C.mu[j] = P.mu;
+    C.mu[j] = PQ[j].mu;
     for (int k = 0; k < kPolyPowMaxPrimes; ++k) C.inv[j][k] = k < j ? (uint32_t)host_powmod(kQ[k] % q, q - 2, q) : 0u;
     const uint32_t w = (uint32_t)host_powmod(kRoot[j], (q - 1) / N, q);   // primitive N-th root
     const uint32_t wi = (uint32_t)host_powmod(w, q - 2, q);
-    const uint32_t ninv = (uint32_t)host_powmod(N, q - 2, q);
-    const TwTab TF = make_tables(twf, w, N, P, st);
-    const TwTab TI = make_tables(twi, wi, N, P, st);
+    ninv[j] = (uint32_t)host_powmod(N, q - 2, q);
+    TF[j] = plan_tables(tw + 2 * kTwWords * (size_t)j, w, N, PQ[j], J, njobs);
+    TI[j] = plan_tables(tw + 2 * kTwWords * (size_t)j + kTwWords, wi, N, PQ[j], J, njobs);
+  }
+  power_tables_kernel<<<dim3(16, njobs), block, 0, st>>>(J);
+  for (int j = 0; j < nprimes; ++j) {
+    const PrimeQ &P = PQ[j];
     zero_kernel<<<grid, block, 0, st>>>(a, N);
     scatter_kernel<<<64, block, 0, st>>>(coeffs_dev, d, B, a, P);
     // forward: outer passes on blocks of M = N, N / 2^kp0, ...; the inner pass fuses the powers and the inverse
     int logM = logN;
     for (int i = 0; i < n_outer; ++i) {
-      ntt_column_pass<false><<<(N >> outer[i]) / kPassCols, block, 0, st>>>(a, logN, logM, outer[i], TF, TF, P);
+      column_pass(false, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TF[j], P, st);
       logM -= outer[i];
     }
-    const uint32_t inner_words = N < (uint32_t)(kPassR * kPassCols) ? N : (uint32_t)(kPassR * kPassCols);
-    ntt_inner_pow<<<N / inner_words, block, 0, st>>>(a, logN, inner, (uint32_t)n, TF, TI, P);
+    if (inner == kPassMaxStages && N >= (uint32_t)(kPassR * kPassCols)) {
+      const uint32_t cn = (uint32_t)host_powmod(2, 32 * (uint64_t)n, P.q);
+      ntt_inner_regs<<<N / (kPassR * kPassCols), kNttThreads, 0, st>>>(a, logN, (uint32_t)n, cn, TF[j], TI[j], P);
+    } else {
+      const uint32_t inner_words = N < (uint32_t)(kPassR * kPassCols) ? N : (uint32_t)(kPassR * kPassCols);
+      ntt_inner_pow<<<N / inner_words, block, 0, st>>>(a, logN, inner, (uint32_t)n, TF[j], TI[j], P);
+    }
     for (int i = n_outer - 1; i >= 0; --i) {
       logM += outer[i];
-      ntt_column_pass<true><<<(N >> outer[i]) / kPassCols, block, 0, st>>>(a, logN, logM, outer[i], TI, TI, P);
+      column_pass(true, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TI[j], P, st);
     }
-    gather_kernel<<<grid, block, 0, st>>>(a, D, B, ninv, res + (size_t)j * n_out, P);
+    gather_kernel<<<grid, block, 0, st>>>(a, D, B, ninv[j], res + (size_t)j * n_out, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -14,6 +14,8 @@ constexpr int kPolyPowLimbs = 8;       // 256-bit output coefficients
 int polypow_primes(uint64_t sum, int n);
 // scratch words for powering a degree-d form to the n-th power with nprimes primes (d n <= 255)
 size_t polypow_scratch_words(int d, int n, int nprimes);
+// transform length and algorithmic device-memory bytes (reads + writes of every kernel) of one powering call
+void polypow_plan(int d, int n, int nprimes, uint64_t *transform_len, uint64_t *bytes);
 // out: C(d n + 3, 3) x kPolyPowLimbs words; coeffs_dev: C(d + 3, 3) words in device memory
 cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev, uint32_t *out, uint32_t *scratch,
                            cudaStream_t st);

@@ -69,6 +69,8 @@ def _lib():
         L.qfs_matmul_mod.argtypes = [c_int, c_int, c_int, c_int, vp, vp, vp, vp]
         L.qfs_poly_power.argtypes = [c_int, vp, c_int, vp, vp]
         L.qfs_int_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        L.qfs_poly_power_info.argtypes = [c_int, vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_uint64)]
         L.qfs_tune_set.argtypes = [c_int, c_int, ctypes.c_size_t]
         L.qfs_tune_get.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -77,7 +79,8 @@ def _lib():
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
-                     "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power", "qfs_int_peaks"):
+                     "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power", "qfs_poly_power_info",
+                     "qfs_int_peaks"):
             getattr(L, name).restype = c_int
         _LIB = L
         load_tile_table()
@@ -230,6 +233,15 @@ def poly_power_limbs(d, coeffs, n, out=None, stream=None, device=None):
     _need_cuda(out, torch.int32, "out")
     _check(_lib().qfs_poly_power(int(d), c.ctypes.data, int(n), out.data_ptr(), _stream(stream)), "qfs_poly_power")
     return out
+
+
+def poly_power_info(d, coeffs, n):
+    """qfs_poly_power_info: {nprimes, transform_len, hbm_bytes} of one poly_power_limbs call (host only)."""
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint32).reshape(-1))
+    npr, tl, hb = ctypes.c_int(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_lib().qfs_poly_power_info(int(d), c.ctypes.data, int(n), ctypes.byref(npr), ctypes.byref(tl),
+                                      ctypes.byref(hb)), "qfs_poly_power_info")
+    return dict(nprimes=npr.value, transform_len=tl.value, hbm_bytes=hb.value)
 
 
 def poly_power(d, coeffs, n, stream=None):

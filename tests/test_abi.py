@@ -59,3 +59,37 @@ def test_binding_fails_loudly_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(TypeError):
         qfs.heights(5, torch.zeros(3, 35, dtype=torch.uint8))
+
+
+def test_poly_power_plan_without_gpu():
+    # host-only plan of the powering: the prime count follows the exact bound (sum of coefficients)^n against the
+    # product of the primes q = c 2^24 + 1 (largest first), the transform length is the power of two >= (d n + 1)^3,
+    # and the byte count is the pass structure: per prime the tables, the cleared and filled input, 2k + 1 passes
+    # reading and writing the buffer (k outer passes of at most 8 stages), the gather; then the remaindering
+    import numpy as np
+    import paper_2502_12428_gb300.qfs as qfs
+    primes = [2130706433, 2113929217, 2013265921, 1811939329, 1711276033, 1224736769, 1107296257]
+    rng = np.random.default_rng(16)
+    f = rng.integers(0, 5, 969).astype(np.uint32)
+    for n in (5, 10, 15):
+        info = qfs.poly_power_info(16, f, n)
+        bound, prod, need = int(f.sum()) ** n, 1, 0
+        while prod <= bound:
+            prod *= primes[need]
+            need += 1
+        assert info["nprimes"] == need
+        B = 16 * n + 1
+        N = 1 << (B ** 3 - 1).bit_length()
+        assert info["transform_len"] == N
+        logN = N.bit_length() - 1
+        inner = min(8, logN)
+        k = -(-(logN - inner) // 8)
+        n_in, n_out = 969, (16 * n + 3) * (16 * n + 2) * (16 * n + 1) // 6
+        R = min(256, N)
+        tables = 2 * 4 * (min(N, 4096) + max(1, N >> 12) + R)
+        per_prime = tables + 4 * N + 8 * n_in + (2 * k + 1) * 8 * N + 8 * n_out
+        assert info["hbm_bytes"] == need * per_prime + n_out * (4 * need + 32)
+    with pytest.raises(RuntimeError):
+        qfs.poly_power_info(16, f, 16)          # degree 256
+    with pytest.raises(RuntimeError):
+        qfs.poly_power_info(1, [2 ** 31] * 4, 8)  # (sum)^n beyond 256 bits
