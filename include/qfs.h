@@ -133,6 +133,25 @@ int qfs_tune_get(int p, int *round_chunks, size_t *ring_bytes, size_t *smem_byte
 int qfs_autotune(int p, int64_t n, const uint8_t *coeffs, int form, int *best_round, size_t *best_ring,
                  float *best_ms);
 
+/* Launch shape of the swept chain (the dp4a and int32 forms' chain products, Algorithm 1's powering) per prime and
+   form, process-wide.  dense_min: the number of tap pairs (u_I, s_I) of f (15 in all) with a nonzero tap from which
+   a quartic's products run every pair, two input slices per loop pass; quartics with fewer skip the zero pairs one
+   slice at a time (16: every quartic skips).  ctas_per_sm: CTAs per SM of the fused launch whose largest prime is
+   p (0: as many as fit; a launch's own qfs_options_t.ctas_per_sm overrides it).  Heights never depend on either.
+   qfs_sweep_tune_set(form, p, 0, 0) restores the defaults (dense_min 12, as many CTAs as fit).  Returns QFS_OK,
+   QFS_ERR_INVALID_P, or QFS_ERR_FORM (form not dp4a or int32, dense_min outside 0 .. 16 or ctas_per_sm outside
+   0 .. 32).  No counterpart in the paper: it is the autotuned shape of the powering step's products. */
+int qfs_sweep_tune_set(int form, int p, int dense_min, int ctas_per_sm);
+int qfs_sweep_tune_get(int form, int p, int *dense_min, int *ctas_per_sm);
+
+/* Times the fused engine (chain power mode, the given form) on n quartics (device, n x 35) for every candidate
+   swept-chain shape of prime p: dense_min in {0, 6, 8, 10, 12, 14, 16} times ctas_per_sm in {1, .., as many as
+   fit}; keeps the fastest (the faster of two timed launches each) with qfs_sweep_tune_set and reports it (best_ms:
+   its launch time).  Synchronous;
+   allocates a scratch output of n bytes.  Returns QFS_ERR_FORM for a form other than dp4a or int32. */
+int qfs_sweep_autotune(int form, int p, int64_t n, const uint8_t *coeffs, int *best_dense_min, int *best_ctas,
+                       float *best_ms);
+
 /* Frees every workspace of every device this process used.  Synchronous. */
 int qfs_shutdown(void);
 

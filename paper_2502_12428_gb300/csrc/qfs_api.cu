@@ -53,6 +53,14 @@ TileConfig tile_for(int p) {
   const TileConfig t = g_tile[p];
   return t.round_chunks > 0 ? t : default_tile(p);
 }
+SweepConfig g_sweep[2][kMaxP + 1];   // per form (int32, dp4a) and prime: swept-chain launch shape (0: defaults)
+
+bool sweep_form(int form) { return form == QFS_FORM_INT32 || form == QFS_FORM_DP4A; }
+SweepConfig sweep_for(int form, int p) {
+  SweepConfig c = sweep_form(form) ? g_sweep[form == QFS_FORM_DP4A][p] : SweepConfig{0, 0};
+  if (c.dense_min == 0) c.dense_min = kDefaultDenseMin;
+  return c;
+}
 int g_last_cuda = 0;
 
 bool valid_p(int p) { return p == 3 || p == 5 || p == 7 || p == 11 || p == 13; }
@@ -231,6 +239,9 @@ int make_plan(DeviceState &S, int form, int max_p, int64_t n_items, const qfs_op
     cudaError_t e = form_occupancy(form, &blocks, plan.smem, form == QFS_FORM_INT8TC && max_p <= 5);
     if (e != cudaSuccess) return cuda_fail(e);
     per_sm = std::max(1, blocks);
+    // a tuned swept-chain shape of the launch's largest prime caps the CTAs per SM
+    const int tuned = sweep_for(form, max_p).ctas_per_sm;
+    if (tuned > 0) per_sm = std::min(per_sm, tuned);
   }
   int64_t grid = (int64_t)S.sms * per_sm;
   if (opts && opts->max_ctas > 0) grid = std::min<int64_t>(grid, opts->max_ctas);
@@ -321,6 +332,7 @@ int qfs_heights_multi_ex(int n_groups, const qfs_group_t *groups, int max_h, con
     prm.g[k].item_begin = begin;
     prm.g[k].tile_round = tile_for(g.p).round_chunks;
     prm.g[k].tile_ring = tile_for(g.p).ring_words;
+    prm.g[k].dense_min = sweep_for(form, g.p).dense_min;
     begin += g.n;
     ++k;
   }
@@ -493,6 +505,89 @@ int qfs_autotune(int p, int64_t n, const uint8_t *coeffs, int form, int *best_ro
   if (rc) return rc;
   if (best_round) *best_round = best_t.round_chunks;
   if (best_ring) *best_ring = 4 * (size_t)best_t.ring_words;
+  if (best_ms) *best_ms = best;
+  return QFS_OK;
+}
+
+int qfs_sweep_tune_set(int form, int p, int dense_min, int ctas_per_sm) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (!sweep_form(form) || dense_min < 0 || dense_min > 16 || ctas_per_sm < 0 || ctas_per_sm > 32)
+    return QFS_ERR_FORM;
+  g_sweep[form == QFS_FORM_DP4A][p] = SweepConfig{dense_min, ctas_per_sm};
+  return QFS_OK;
+}
+
+int qfs_sweep_tune_get(int form, int p, int *dense_min, int *ctas_per_sm) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (!sweep_form(form)) return QFS_ERR_FORM;
+  const SweepConfig c = sweep_for(form, p);
+  if (dense_min) *dense_min = c.dense_min;
+  if (ctas_per_sm) *ctas_per_sm = c.ctas_per_sm;
+  return QFS_OK;
+}
+
+int qfs_sweep_autotune(int form, int p, int64_t n, const uint8_t *coeffs, int *best_dense_min, int *best_ctas,
+                       float *best_ms) {
+  if (!valid_p(p)) return QFS_ERR_INVALID_P;
+  if (!sweep_form(form)) return QFS_ERR_FORM;
+  if (n <= 0) return QFS_ERR_INVALID_N;
+  if (!coeffs) return QFS_ERR_NULL;
+  int8_t *out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int dense[] = {0, 6, 8, 10, 12, 14, 16};
+  SweepConfig &slot = g_sweep[form == QFS_FORM_DP4A][p];
+  const SweepConfig saved = slot;
+  // the CTAs per SM that fit: the occupancy of the launch a default shape would make
+  slot = SweepConfig{0, 0};
+  int max_ctas = 1;
+  {
+    const size_t smem = ring_offset_for(tet(4 * (p - 1) + 1)) +
+                        4 * (size_t)ring_words_for(p, tile_for(p), uses_ring_chain(form, p), QFS_POWER_CHAIN);
+    int blocks = 0;
+    if (form_occupancy(form, &blocks, smem, false) == cudaSuccess) max_ctas = std::max(1, blocks);
+  }
+  float best = 1e30f;
+  SweepConfig best_c = saved;
+  int rc = QFS_OK;
+  qfs_options_t opt;
+  memset(&opt, 0, sizeof(opt));
+  opt.form = form;
+  opt.engine = QFS_ENGINE_FUSED;
+  opt.power = QFS_POWER_CHAIN;
+  qfs_group_t g{p, n, coeffs, out};
+  for (int dm : dense)
+    for (int c = 1; c <= max_ctas && rc == QFS_OK; ++c) {
+      slot = SweepConfig{dm, c};
+      rc = qfs_heights_multi_ex(1, &g, 10, &opt, 0);  // warm-up
+      if (rc) break;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && rc == QFS_OK; ++rep) {   // the faster of two timed launches
+        cudaEventRecord(a, 0);
+        rc = qfs_heights_multi_ex(1, &g, 10, &opt, 0);
+        cudaEventRecord(b, 0);
+        if (rc) break;
+        cudaEventSynchronize(b);
+        float t = 0;
+        cudaEventElapsedTime(&t, a, b);
+        ms = std::min(ms, t);
+      }
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        best_c = slot;
+      }
+    }
+  slot = rc ? saved : best_c;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (rc) return rc;
+  if (best_dense_min) *best_dense_min = best_c.dense_min;
+  if (best_ctas) *best_ctas = best_c.ctas_per_sm;
   if (best_ms) *best_ms = best;
   return QFS_OK;
 }

@@ -46,6 +46,7 @@ struct Smem {
   int taps[35];           // coefficients of f, packed order (index tet(uI) + tri(sI) + tI)
   uint32_t tapword[15];   // dp4a tap words per (uI, sI) pair: byte k = a(uI, sI, 3-k)
   uint32_t pair_mask;     // bit tri(uI)+sI set iff that pair has a nonzero tap
+  int dense_min;          // nonzero tap pairs from which the swept chain runs every pair (the two-slice loop)
   int powp[kMaxP];        // c^p mod p^2
   int slot_tab[2][kMaxUparDecl + 4];  // ring word offsets of the slices a chain round reads (double buffered)
   uint16_t chunk_tab[32 * 40];        // chain block: flat chunk index -> (column - s0) << 8 | chunk

@@ -50,6 +50,15 @@ struct TileConfig {
   int ring_words;
 };
 
+// Swept-chain launch shape of one prime and form (dp4a, int32): dense_min = nonzero tap pairs (of 15) from which
+// a quartic takes the every-pair path (16: never), ctas_per_sm = CTAs per SM of the fused launch (0: as many as
+// fit).  Results never depend on either.
+constexpr int kDefaultDenseMin = 12;
+struct SweepConfig {
+  int dense_min;
+  int ctas_per_sm;
+};
+
 __host__ __device__ inline TileConfig default_tile(int p) {
   return TileConfig{kDefaultRoundChunks, p <= 7 ? kRingBudgetSmallP : kRingBudgetLargeP};
 }
@@ -1639,6 +1648,7 @@ struct FusedGroup {
   int8_t *heights;
   int64_t item_begin;
   int tile_round, tile_ring;
+  int dense_min;
 };
 
 constexpr int kMaxGroups = 8;
@@ -1693,6 +1703,7 @@ __device__ __forceinline__ void fused_body(const FusedParams &prm) {
     if (threadIdx.x == 0) {
       sm.tile_round = G.tile_round;
       sm.tile_ring = G.tile_ring;
+      sm.dense_min = G.dense_min;
     }
     const uint8_t *f = G.coeffs + 35 * row;
     int h, steps;

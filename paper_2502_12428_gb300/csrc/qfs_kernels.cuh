@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kThreads) debug_kernel(const uint8_t *f, int m
   if (threadIdx.x == 0) {
     sm.tile_round = default_tile(P).round_chunks;
     sm.tile_ring = default_tile(P).ring_words;
+    sm.dense_min = kDefaultDenseMin;
   }
   __syncthreads();
   int steps = 0;

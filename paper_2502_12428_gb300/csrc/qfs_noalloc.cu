@@ -137,6 +137,7 @@ extern "C" int qfs_heights_noalloc(int p, int64_t n, const uint8_t *coeffs, int 
   prm.g[0].item_begin = 0;
   prm.g[0].tile_round = default_tile(p).round_chunks;
   prm.g[0].tile_ring = default_tile(p).ring_words;
+  prm.g[0].dense_min = kDefaultDenseMin;
   prm.n_groups = 1;
   prm.n_items = n;
   prm.max_h = max_h;

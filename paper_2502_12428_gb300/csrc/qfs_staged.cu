@@ -50,6 +50,7 @@ __device__ __forceinline__ void stage_smem(Smem *&sm, uint8_t *&gs, uint8_t *&gn
   if (threadIdx.x == 0) {
     sm->tile_round = default_tile(P).round_chunks;
     sm->tile_ring = default_tile(P).ring_words;
+    sm->dense_min = kDefaultDenseMin;
   }
   gs = smem_raw + sizeof(Smem);
   gn = gs + Prime<P>::ld;

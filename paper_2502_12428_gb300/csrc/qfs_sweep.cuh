@@ -402,15 +402,16 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
 
 }  // namespace sweep
 
-// Entry point used by chain_step for the dp4a (FORM 1) and int32 (FORM 0) forms.  Quartics with few zero tap
-// pairs run every pair; the others skip zero pairs (and input columns none of whose pairs is nonzero).
+// Entry point used by chain_step for the dp4a (FORM 1) and int32 (FORM 0) forms.  Quartics with at least
+// sm.dense_min nonzero tap pairs (of 15) run every pair; the others skip zero pairs (and input columns none of whose
+// pairs is nonzero).  The threshold is a per-prime tuning parameter (kDefaultDenseMin unless tuned).
 // The caller runs it with every warp of the CTA, between two barriers, with sm.task_next and sm.task_done zero
 // (init_task_queue at kernel start; run_tasks leaves them zero).
 template <int P, int FORM, bool LAST, bool DEBUG>
 __device__ __forceinline__ void sweep_chain_step(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                  int m_in, Smem &sm, const uint8_t *gs, uint32_t *status,
                                                  DebugPtrs dbg) {
-  if (__popc(sm.pair_mask) >= 12)
+  if (__popc(sm.pair_mask) >= sm.dense_min)
     sweep::run_tasks<P, FORM, true, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);
   else
     sweep::run_tasks<P, FORM, false, LAST, DEBUG>(in, out, m_in, sm, gs, status, dbg);

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(kThreads, 1) theta_delta_kernel(const uint8_t 
   if (threadIdx.x == 0) {
     sm.tile_round = default_tile(P).round_chunks;
     sm.tile_ring = default_tile(P).ring_words;
+    sm.dense_min = kDefaultDenseMin;
   }
   uint32_t *bufA, *bufB;
   cta_buffers(ws, stride, bufA, bufB);

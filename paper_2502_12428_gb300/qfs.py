@@ -76,9 +76,14 @@ def _lib():
                                    ctypes.POINTER(ctypes.c_size_t)]
         L.qfs_autotune.argtypes = [c_int, i64, vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_float)]
+        L.qfs_sweep_tune_set.argtypes = [c_int, c_int, c_int, c_int]
+        L.qfs_sweep_tune_get.argtypes = [c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        L.qfs_sweep_autotune.argtypes = [c_int, c_int, i64, vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                         ctypes.POINTER(ctypes.c_float)]
         for name in ("qfs_heights", "qfs_heights_multi", "qfs_heights_multi_ex", "qfs_set_default_form",
                      "qfs_plan_prepare", "qfs_shutdown", "qfs_read_status", "qfs_read_stats", "qfs_last_cuda_error",
                      "qfs_debug_stages", "qfs_heights_noalloc", "qfs_tune_set", "qfs_tune_get", "qfs_autotune",
+                     "qfs_sweep_tune_set", "qfs_sweep_tune_get", "qfs_sweep_autotune",
                      "qfs_theta_matrix", "qfs_matmul_mod", "qfs_poly_power", "qfs_poly_power_info",
                      "qfs_int_peaks"):
             getattr(L, name).restype = c_int
@@ -284,15 +289,44 @@ def save_tile_table(entries, path=TILE_TABLE):
         json.dump({str(k): v for k, v in entries.items()}, fh, indent=1, sort_keys=True)
 
 
+def _form_id(form):
+    return FORMS[form] if isinstance(form, str) else int(form)
+
+
+def sweep_tune_set(form, p, dense_min, ctas_per_sm):
+    """qfs_sweep_tune_set: swept-chain shape of (form, p); (0, 0) restores the defaults."""
+    _check(_lib().qfs_sweep_tune_set(_form_id(form), int(p), int(dense_min), int(ctas_per_sm)), "qfs_sweep_tune_set")
+
+
+def sweep_tune_get(form, p):
+    dm, c = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib().qfs_sweep_tune_get(_form_id(form), int(p), ctypes.byref(dm), ctypes.byref(c)), "qfs_sweep_tune_get")
+    return dict(dense_min=dm.value, ctas_per_sm=c.value)
+
+
+def sweep_autotune(p, sample, form="dp4a"):
+    """Times every candidate swept-chain shape (dense threshold x CTAs per SM) on `sample` (CUDA uint8 n x 35) and
+    keeps the fastest for (form, p)."""
+    _need_cuda(sample, torch.uint8, "sample")
+    dm, c, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
+    _check(_lib().qfs_sweep_autotune(_form_id(form), int(p), int(sample.shape[0]), sample.data_ptr(),
+                                     ctypes.byref(dm), ctypes.byref(c), ctypes.byref(ms)), "qfs_sweep_autotune")
+    return dict(dense_min=dm.value, ctas_per_sm=c.value, ms=ms.value)
+
+
 def load_tile_table(path=TILE_TABLE):
-    """Applies a persisted tile table (missing file: nothing to do).  Returns the entries applied."""
+    """Applies a persisted tile table (missing file: nothing to do): per prime the ring tile of the int8 tensor
+    form, and under "sweep" the swept-chain shape of each of the dp4a and int32 forms.  Returns the entries."""
     import json
     if not os.path.exists(path):
         return {}
     with open(path) as fh:
         table = json.load(fh)
     for p, v in table.items():
-        tune_set(int(p), v["round_chunks"], v["ring_bytes"])
+        if "round_chunks" in v:
+            tune_set(int(p), v["round_chunks"], v["ring_bytes"])
+        for form, sw in v.get("sweep", {}).items():
+            sweep_tune_set(form, int(p), sw["dense_min"], sw["ctas_per_sm"])
     return table
 
 

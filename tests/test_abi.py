@@ -93,3 +93,22 @@ def test_poly_power_plan_without_gpu():
         qfs.poly_power_info(16, f, 16)          # degree 256
     with pytest.raises(RuntimeError):
         qfs.poly_power_info(1, [2 ** 31] * 4, 8)  # (sum)^n beyond 256 bits
+
+
+def test_sweep_tuning_argument_checks_without_gpu(libqfs):
+    # the swept-chain shape is host state: set, read back and validated without any CUDA call
+    st, gt = libqfs.qfs_sweep_tune_set, libqfs.qfs_sweep_tune_get
+    st.argtypes = [ctypes.c_int] * 4
+    gt.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    st.restype = gt.restype = ctypes.c_int
+    dm, c = ctypes.c_int(-1), ctypes.c_int(-1)
+    assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (12, 0)
+    assert st(1, 7, 9, 1) == 0
+    assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (9, 1)
+    assert gt(0, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (12, 0)   # per form
+    assert st(1, 7, 0, 0) == 0
+    assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (12, 0)
+    assert st(1, 4, 9, 1) == 1          # invalid p
+    assert st(2, 7, 9, 1) == 7          # the tensor form has no swept chain
+    assert st(1, 7, 17, 1) == 7 and st(1, 7, 9, 33) == 7
+

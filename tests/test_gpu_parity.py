@@ -350,6 +350,32 @@ def test_tile_shapes_do_not_change_heights(qfs):
         qfs.tune_set(p, saved["round_chunks"], saved["ring_bytes"])
 
 
+@pytest.mark.parametrize("form", ["dp4a", "int32"])
+def test_sweep_shapes_do_not_change_heights(qfs, form):
+    # the swept chain's dense threshold decides, per quartic, between the every-pair two-slice loop and the
+    # zero-pair-skipping one-slice loop; mixed dense and sparse rows take both paths under every threshold
+    p = 5
+    f = np.concatenate([inputs.dense(p, 700, 6610), inputs.sparse(p, 1300, 6611)])
+    t = dev_tensor(f)
+    want = oracle.heights(p, f)
+    saved = qfs.sweep_tune_get(form, p)
+    try:
+        for dm, ctas in [(0, 2), (16, 1), (8, 0), (12, 1)]:
+            qfs.sweep_tune_set(form, p, dm, ctas)
+            assert qfs.sweep_tune_get(form, p) == {"dense_min": dm if dm else 12, "ctas_per_sm": ctas}
+            assert np.array_equal(qfs.heights(p, t, form=form).cpu().numpy(), want)
+        with pytest.raises(qfs.QfsError):
+            qfs.sweep_tune_set(form, p, 17, 0)
+        with pytest.raises(qfs.QfsError):
+            qfs.sweep_tune_set("int8tc", p, 8, 0)
+        best = qfs.sweep_autotune(p, t[:600], form=form)
+        assert 0 <= best["dense_min"] <= 16 and best["ctas_per_sm"] >= 1 and best["ms"] > 0
+        assert qfs.sweep_tune_get(form, p)["ctas_per_sm"] == best["ctas_per_sm"]
+        assert np.array_equal(qfs.heights(p, t, form=form).cpu().numpy(), want)
+    finally:
+        qfs.sweep_tune_set(form, p, saved["dense_min"], saved["ctas_per_sm"])
+
+
 def test_cuda_graph_capture_and_replay(qfs):
     # the call is stream-ordered and allocation-free once the workspace exists, so it can be captured
     p = 5
