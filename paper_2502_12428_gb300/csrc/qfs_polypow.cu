@@ -8,10 +8,11 @@
 //   2. For each of P word-size primes q = c 2^24 + 1: reduce the coefficients mod q, forward transform
 //      (Gentleman-Sande, natural order in, bit-reversed order out), raise every entry to the n-th power, inverse
 //      transform (Cooley-Tukey, bit-reversed in, natural out), and gather the coefficients of the degree-d n output
-//      monomials (times N^-1).  The transforms run in passes of up to 8 radix-2 stages in shared memory (the
-//      four-step split of a length-M transform into R-point transforms over columns of stride M / R, twiddles
-//      w_M^(c k) between passes); the last forward pass, the n-th powers and the first inverse pass share one
-//      kernel, so a length-2^24 transform pair costs five round trips through device memory instead of 48.
+//      monomials (times N^-1).  The transforms run in passes of up to 8 radix-2 stages (the four-step split of a
+//      length-M transform into R-point transforms over columns of stride M / R, twiddles w_M^(c k) between
+//      passes); inside a pass the stages run in registers in two groups with one exchange through shared memory
+//      between them.  The last forward pass, the n-th powers and the first inverse pass share one kernel, so a
+//      length-2^24 transform pair costs five round trips through device memory instead of 48.
 //   3. Chinese remaindering (Garner's mixed-radix form) of the P residues of every coefficient into a 256-bit
 //      unsigned integer.  P is the smallest number of primes whose product exceeds the coefficient bound
 //      (sum of |coefficients|)^n, so the result is exact.
