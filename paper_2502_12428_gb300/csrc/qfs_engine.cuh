@@ -732,27 +732,31 @@ __device__ __noinline__ bool theta_gather(const uint32_t *__restrict__ dg, const
 // output r = (u_r, s_r, t_r) of this lane: each column s_c inside the lane's range [lo, hi] adds the lane's Delta
 // window (NW + 1 words of the guarded slot, shifted to the window's first byte) against the NW words of g's
 // reversed column s_c, which are the same for every lane.  ebase = p s_r + 2(p-1), so the Delta column is
-// e_s = ebase - s_c; tbase = p t_r + (p-1), the window's last byte in that column.  All loads of the four columns
-// are issued before the first product.
+// e_s = ebase - s_c; tbase = p t_r + (p-1), the window's last byte in that column.  A column without a term for
+// this lane reads its window from the zero guard words at the start of the slot (kThetaGuardWords >= NW + 1), so
+// no load is predicated: its g words are then multiplied by zeros whatever they hold (past sc1 they are words of
+// the next reversed columns or of the table after them, inside the ring).  The g column offset advances by NW
+// words per column (rcolw(s + 1) - rcolw(s) = s / 4 + 1).  All loads of the four columns are issued before the
+// first product.
 template <int P, int NW>
 __device__ __forceinline__ unsigned theta_seg(const uint32_t *__restrict__ slot, const uint32_t *__restrict__ Rb,
                                               const int *__restrict__ gofs, int sc0, int sc1, int lo, int hi,
                                               int ebase, int tbase, unsigned a) {
+  static_assert(kThetaGuardWords >= NW + 1, "a window read from the zero guard stays inside it");
   uint32_t dv[4][NW + 1], rv[4][NW];
   unsigned sh[4];
+  const uint32_t *rw = Rb + rcolw(sc0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int sc = sc0 + j;
-    const bool in = sc <= sc1;
-    const bool on = in && sc >= lo && sc <= hi;
+    const bool on = sc <= sc1 && sc >= lo && sc <= hi;
     const int byte = on ? gofs[ebase - sc] + tbase - sc : 0;
     sh[j] = 8u * (unsigned)(byte & 3);
     const uint32_t *dw = slot + (byte >> 2);
 #pragma unroll
-    for (int k = 0; k <= NW; ++k) dv[j][k] = on ? dw[k] : 0u;
-    const uint32_t *rw = Rb + rcolw(sc);
+    for (int k = 0; k <= NW; ++k) dv[j][k] = dw[k];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) rv[j][k] = in ? rw[k] : 0u;
+    for (int k = 0; k < NW; ++k) rv[j][k] = rw[NW * j + k];
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j)
