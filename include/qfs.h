@@ -147,7 +147,8 @@ int qfs_sweep_tune_get(int form, int p, int *dense_min, int *ctas_per_sm);
 /* Times the fused engine (chain power mode, the given form) on n quartics (device, n x 35) for every candidate
    swept-chain shape of prime p: dense_min in {0, 6, 8, 10, 12, 14, 16} times ctas_per_sm in {1, .., as many as
    fit}; keeps the fastest (the faster of two timed launches each) with qfs_sweep_tune_set and reports it (best_ms:
-   its launch time).  Synchronous;
+   its launch time; best_ctas 0 when the fastest was the most CTAs that fit, so that the setting never caps a launch
+   with other primes, which may fit more).  Synchronous;
    allocates a scratch output of n bytes.  Returns QFS_ERR_FORM for a form other than dp4a or int32. */
 int qfs_sweep_autotune(int form, int p, int64_t n, const uint8_t *coeffs, int *best_dense_min, int *best_ctas,
                        float *best_ms);

@@ -581,6 +581,9 @@ int qfs_sweep_autotune(int form, int p, int64_t n, const uint8_t *coeffs, int *b
         best_c = slot;
       }
     }
+  // the largest count that fit is stored as 0 ("as many as fit"): a launch with other primes may fit more CTAs,
+  // and a shape tuned on this prime alone must not cap it
+  if (best_c.ctas_per_sm == max_ctas) best_c.ctas_per_sm = 0;
   slot = rc ? saved : best_c;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

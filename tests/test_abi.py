@@ -102,6 +102,13 @@ def test_sweep_tuning_argument_checks_without_gpu(libqfs):
     gt.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     st.restype = gt.restype = ctypes.c_int
     dm, c = ctypes.c_int(-1), ctypes.c_int(-1)
+    # the state is process-wide (the binding may have applied a tuned table already): save, reset, restore
+    assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0
+    saved = [(f, ) + tuple(v.value for v in (dm, c)) for f in (1,)]
+    d0, c0 = ctypes.c_int(-1), ctypes.c_int(-1)
+    assert gt(0, 7, ctypes.byref(d0), ctypes.byref(c0)) == 0
+    saved.append((0, d0.value, c0.value))
+    assert st(1, 7, 0, 0) == 0 and st(0, 7, 0, 0) == 0
     assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (12, 0)
     assert st(1, 7, 9, 1) == 0
     assert gt(1, 7, ctypes.byref(dm), ctypes.byref(c)) == 0 and (dm.value, c.value) == (9, 1)
@@ -111,4 +118,6 @@ def test_sweep_tuning_argument_checks_without_gpu(libqfs):
     assert st(1, 4, 9, 1) == 1          # invalid p
     assert st(2, 7, 9, 1) == 7          # the tensor form has no swept chain
     assert st(1, 7, 17, 1) == 7 and st(1, 7, 9, 33) == 7
+    for f, d, n in saved:
+        assert st(f, 7, d, n) == 0
 

@@ -369,7 +369,7 @@ def test_sweep_shapes_do_not_change_heights(qfs, form):
         with pytest.raises(qfs.QfsError):
             qfs.sweep_tune_set("int8tc", p, 8, 0)
         best = qfs.sweep_autotune(p, t[:600], form=form)
-        assert 0 <= best["dense_min"] <= 16 and best["ctas_per_sm"] >= 1 and best["ms"] > 0
+        assert 0 <= best["dense_min"] <= 16 and best["ctas_per_sm"] >= 0 and best["ms"] > 0
         assert qfs.sweep_tune_get(form, p)["ctas_per_sm"] == best["ctas_per_sm"]
         assert np.array_equal(qfs.heights(p, t, form=form).cpu().numpy(), want)
     finally:
