@@ -74,8 +74,8 @@ __host__ __device__ inline ChainTile chain_tile(int s0, int m_out, TileConfig tc
   T.stride = 4 * (T.CR + 1);
   T.slot_words = 36 * T.stride;
   const int per_slice = chunk_prefix(s_hi + 1) - chunk_prefix(s0);
-  int up = (tc.round_chunks + per_slice - 1) / per_slice;
-  up = max(1, min(kMaxUpar, up));
+  int up = 1;   // ceil(round_chunks / per_slice), at most kMaxUpar, counted up (no runtime division)
+  while (up < kMaxUpar && up * per_slice < tc.round_chunks) ++up;
   while (up > 1 && (2 * up + 4) * T.slot_words > tc.ring_words) --up;
   T.upar = up;
   T.nslot = 2 * up + 4;
@@ -289,18 +289,20 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
       const bool slice_ok = u2 >= 0 && u2 <= m_in;
       const int base_u = slice_ok ? sm.SW[u2] : 0;
       for (int i = threadIdx.x; i < 36 * ccols; i += nthreads) {
-        const int cs = i / ccols, j = i - cs * ccols;
+        const int cs = small_quotient<6>(i, ccols), j = i - cs * ccols;   // i < 36 ccols
         const int s2 = s0 - 4 + cs;
         const bool ok = slice_ok && j >= 1 && s2 >= 0 && s2 <= u2 && j - 1 < chunks_of(s2);
         const uint32_t *src = ok ? in + base_u + colw(s2) + 4 * (j - 1) : in;
         cp_async16(dst + cs * T.stride + 4 * j, src, ok);
       }
     };
-    for (int u2 = s0 - 4; u2 < s0 + T.upar; ++u2) fetch(u2, (u2 - s0 + 4) % T.nslot);
+    // ring slot of slice u2: (u2 - s0 + 4) mod nslot (u2 - s0 + 4 <= D + 4 < 2^7 nslot)
+    auto slot_of = [&](int u2) { const int x = u2 - s0 + 4; return x - small_quotient<7>(x, T.nslot) * T.nslot; };
+    for (int u2 = s0 - 4; u2 < s0 + T.upar; ++u2) fetch(u2, slot_of(u2));
     cp_async_commit();
     if (threadIdx.x < kMaxUpar + 4) {
       const int u2 = s0 - 4 + (int)threadIdx.x;
-      sm.slot_tab[0][threadIdx.x] = ((u2 - s0 + 4) % T.nslot) * T.slot_words;
+      sm.slot_tab[0][threadIdx.x] = slot_of(u2) * T.slot_words;
     }
     for (int s = s0 + (int)threadIdx.x; s <= s_last; s += nthreads) {
       const int base = chunk_prefix(s) - F0;
@@ -310,11 +312,11 @@ __device__ __forceinline__ void ring_chain_step(const uint32_t *__restrict__ in,
     __syncthreads();
     int tab = 0;
     for (int u = s0; u <= m_out; u += T.upar) {
-      for (int u2 = u + T.upar; u2 < u + 2 * T.upar && u2 <= m_out; ++u2) fetch(u2, (u2 - s0 + 4) % T.nslot);
+      for (int u2 = u + T.upar; u2 < u + 2 * T.upar && u2 <= m_out; ++u2) fetch(u2, slot_of(u2));
       cp_async_commit();
       if (threadIdx.x < kMaxUpar + 4) {  // slot table of the next round (slices u + upar - 4 ..)
         const int u2 = u + T.upar - 4 + (int)threadIdx.x;
-        sm.slot_tab[tab ^ 1][threadIdx.x] = ((u2 - s0 + 4) % T.nslot) * T.slot_words;
+        sm.slot_tab[tab ^ 1][threadIdx.x] = slot_of(u2) * T.slot_words;
       }
       const int nU = min(T.upar, m_out - u + 1);
       // chunk prefix over the round's slices: slice u+du holds columns s0 .. min(s_last, u+du)

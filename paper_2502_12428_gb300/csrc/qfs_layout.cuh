@@ -122,6 +122,17 @@ __device__ __forceinline__ void build_sw(int *SW, int n) {
   }
 }
 
+// floor(x / m) for 0 <= x < 2^K m, m >= 1, by K compare-and-add steps (no division: a runtime divisor would be
+// lowered through the floating-point reciprocal unit).
+template <int K>
+__host__ __device__ __forceinline__ int small_quotient(int x, int m) {
+  int q = 0;
+#pragma unroll
+  for (int b = K - 1; b >= 0; --b)
+    if (x >= (q + (1 << b)) * m) q += 1 << b;
+  return q;
+}
+
 // Flat chunk index h of one slice (h = F(s) + c) -> column s and chunk c.  F(s) = E(s+4) - 4, so h + 4 is the
 // flat index of chunk c of "column" s + 4 under E, which inverts in closed form.
 __host__ __device__ inline void decode_chunk(int h, int &s, int &c) {
@@ -131,7 +142,7 @@ __host__ __device__ inline void decode_chunk(int h, int &s, int &c) {
   while (8 * (q + 1) * (q + 2) <= h) ++q;
   while (q > 0 && 8 * q * (q + 1) > h) --q;
   const int rem = h - 8 * q * (q + 1);
-  const int rr = rem / (q + 1);
+  const int rr = small_quotient<4>(rem, q + 1);   // rem < 16 (q + 1)
   c = rem - rr * (q + 1);
   s = 16 * q + rr - 4;
 }

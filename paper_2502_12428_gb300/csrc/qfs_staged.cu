@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(kThreads) stage_delta1(StagedChunk c) {
   const size_t gwords = c.ws_words;            // stride of the G slots
   const size_t chunks = (size_t)SW[Pr::D + 1] / 4;  // 16-byte chunks of a degree-D form (the slot may be longer)
   bool bad = false;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)total * chunks;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t slot = i / chunks, k = i - slot * chunks;
+  // slots by block, chunks by thread (no 64-bit division of a flat index)
+  for (size_t slot = blockIdx.x; slot < total; slot += gridDim.x)
+  for (size_t k = threadIdx.x; k < chunks; k += blockDim.x) {
     int u, s, ch;
     decode_form_chunk((int)k, Pr::D, SW, u, s, ch);
     uint4 *p4 = reinterpret_cast<uint4 *>(c.G + slot * gwords + 4 * k);

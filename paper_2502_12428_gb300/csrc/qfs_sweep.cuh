@@ -33,7 +33,7 @@ __host__ __device__ inline void decode_half(int i, int &s, int &h) {
   while (4 * (a + 1) * (a + 2) <= i) ++a;
   while (a > 0 && 4 * a * (a + 1) > i) --a;
   const int rem = i - 4 * a * (a + 1);
-  const int b = rem / (a + 1);
+  const int b = small_quotient<3>(rem, a + 1);   // rem < 8 (a + 1)
   h = rem - b * (a + 1);
   s = 8 * a + b;
 }
@@ -53,8 +53,8 @@ namespace sweep {
 struct Lane {
   int s, h;
   int off[5];      // word offset of input column s - sI, half-chunk h, inside a slice
+  int first[5];    // first input slice holding column s - sI (s - sI; past every slice if the column or item does not exist)
   int out_off;     // word offset of the output half-chunk inside a slice
-  uint32_t colok;  // bit sI: the item exists and s - sI >= 0
   int pad;         // half-chunks of zero padding after this item that this lane writes (0, 1 or 2)
   bool valid;      // the item exists
 };
@@ -69,7 +69,7 @@ __device__ __forceinline__ void load_slice(const uint32_t *__restrict__ in, cons
   const int base = sm.SW[max(v, 0)];  // v = -1 (a leading slice with no columns) reads only guard words
 #pragma unroll
   for (int sI = 0; sI < 5; ++sI) {
-    const bool ex = ((L.colok >> sI) & 1u) && (L.s - sI <= v);
+    const bool ex = v >= L.first[sI];
     const uint32_t *q = in + (ex ? base + L.off[sI] : -2);
     const uint2 w = *reinterpret_cast<const uint2 *>(q);
     X[sI][0] = q[-1];
@@ -327,11 +327,10 @@ __device__ __noinline__ void run_tasks(const uint32_t *__restrict__ in, uint32_t
     L.valid = i < n_items;
     decode_half(L.valid ? i : n_items - 1, L.s, L.h);
     const int s_first = __shfl_sync(0xffffffffu, L.s, 0);
-    L.colok = 0;
 #pragma unroll
     for (int sI = 0; sI < 5; ++sI) {
       const int sc = L.s - sI;
-      if (L.valid && sc >= 0) L.colok |= 1u << sI;
+      L.first[sI] = L.valid && sc >= 0 ? sc : 1 << 30;
       L.off[sI] = colw(max(sc, 0)) + 2 * L.h;
     }
     L.out_off = colw(L.s) + 2 * L.h;
