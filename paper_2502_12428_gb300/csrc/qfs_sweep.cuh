@@ -156,13 +156,14 @@ __device__ __forceinline__ void column_windows(const uint32_t (&X)[3], uint32_t 
 template <int J>
 __device__ __forceinline__ void slice_macs_merged(const uint32_t (&X)[5][3], const uint32_t (&tw)[15], uint32_t a44,
                                                   int (&acc)[6][8]) {
-  uint32_t W0[2][4];
-  column_windows(X[0], W0);
+  // pair (0, 0) has the single tap a(0,0,0) (byte 3 of tw[0]) on in_0(t), which is byte r of word q + 1 of
+  // column 0: no window, a dp4a against the tap shifted to byte r
+  const uint32_t a00 = tw[0] >> 24;
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      acc[J][4 * q + r] = (int)__dp4a(W0[q][r], tw[0], (unsigned)acc[J][4 * q + r]);
+      acc[J][4 * q + r] = (int)__dp4a(X[0][q + 1], a00 << (8 * r), (unsigned)acc[J][4 * q + r]);
   {
     uint32_t W1[2][4];
     column_windows(X[1], W1);
@@ -170,7 +171,7 @@ __device__ __forceinline__ void slice_macs_merged(const uint32_t (&X)[5][3], con
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const uint32_t m = __byte_perm(W1[q][r], W0[q][r], 0x3217u);
+        const uint32_t m = __byte_perm(W1[q][r], X[0][q + 1], 0x3214u + r);   // byte 0 <- in_0(t)
         acc[J + 1][4 * q + r] = (int)__dp4a(m, tw[2], (unsigned)acc[J + 1][4 * q + r]);
       }
 #pragma unroll
@@ -188,7 +189,7 @@ __device__ __forceinline__ void slice_macs_merged(const uint32_t (&X)[5][3], con
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const uint32_t m = __byte_perm(W2[q][r], W0[q][r], 0x3217u);
+        const uint32_t m = __byte_perm(W2[q][r], X[0][q + 1], 0x3214u + r);   // byte 0 <- in_0(t)
 #pragma unroll
         for (int uI = 2; uI < 5; ++uI)
           acc[J + uI][4 * q + r] = (int)__dp4a(m, tw[tri(uI) + 2], (unsigned)acc[J + uI][4 * q + r]);
