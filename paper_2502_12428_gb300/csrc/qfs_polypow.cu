@@ -399,9 +399,11 @@ __device__ __forceinline__ uint32_t column_twiddle(uint32_t x, const uint32_t *p
 // rows m0 + (k << K2) of column cc, a task (cc, g) rows (g << K2) + r; the lanes of a warp are 32 consecutive
 // columns, so every global access is one 128-byte row segment and every shared-memory access is free of conflicts
 // (row stride kPassCols + 1).
+// nz_rows (forward): rows m >= nz_rows of every column are zero and are not read (the first pass of a transform
+// whose input fills only its leading rows).
 template <int KP, bool INV>
 __global__ void __launch_bounds__(kNttThreads) ntt_column_regs(uint32_t *a, int logN, int logM, TwTab T, TwTab TR,
-                                                               PrimeQ P) {
+                                                               PrimeQ P, int nz_rows) {
   static_assert(KP >= 2 && KP <= kPassMaxStages, "two register phases");
   constexpr int K1 = KP / 2, K2 = KP - K1, ld = kPassCols + 1;
   constexpr int NT1 = kPassCols << K2, NT2 = kPassCols << K1;   // tasks of the strided and the contiguous phase
@@ -424,7 +426,10 @@ __global__ void __launch_bounds__(kNttThreads) ntt_column_regs(uint32_t *a, int 
         const int cc = task & (kPassCols - 1), m0 = task >> 5;
         uint32_t x[1 << K1];
 #pragma unroll
-        for (int k = 0; k < (1 << K1); ++k) x[k] = col[cc + (size_t)(m0 + (k << K2)) * Nc];
+        for (int k = 0; k < (1 << K1); ++k) {
+          const int m = m0 + (k << K2);
+          x[k] = m < nz_rows ? col[cc + (size_t)m * Nc] : 0u;
+        }
         reg_dif<KP, K1, K2, false>(x, m0, rt, rts, P.q);
 #pragma unroll
         for (int k = 0; k < (1 << K1); ++k) tile[(m0 + (k << K2)) * ld + cc] = x[k];
@@ -579,13 +584,17 @@ struct CrtParams {
 };
 
 // Garner: v_j = (...((r_j - v_0) q_0^-1 - v_1) q_1^-1 ... - v_{j-1}) q_{j-1}^-1 mod q_j; then
-// X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) in 8 little-endian 32-bit limbs
+// X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) in 8 little-endian 32-bit limbs.  v_k mod q_j for k < j is one conditional
+// subtraction: the primes are taken largest first and the largest is below twice the smallest, so v_k < 2 q_j.
 __global__ void crt_kernel(const uint32_t *res, int n_out, CrtParams C, uint32_t *out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_out; i += gridDim.x * blockDim.x) {
     uint32_t v[kPolyPowMaxPrimes];
     for (int j = 0; j < C.nprimes; ++j) {
       uint32_t t = res[(size_t)j * n_out + i];
-      for (int k = 0; k < j; ++k) t = mulmod(submod(t, v[k] % C.q[j], C.q[j]), C.inv[j][k], C.q[j], C.mu[j]);
+      for (int k = 0; k < j; ++k) {
+        const uint32_t vk = v[k] >= C.q[j] ? v[k] - C.q[j] : v[k];
+        t = mulmod(submod(t, vk, C.q[j]), C.inv[j][k], C.q[j], C.mu[j]);
+      }
       v[j] = t;
     }
     uint32_t x[kPolyPowLimbs];
@@ -607,6 +616,7 @@ __global__ void crt_kernel(const uint32_t *res, int n_out, CrtParams C, uint32_t
 constexpr uint32_t kQ[kPolyPowMaxPrimes] = {2130706433u, 2113929217u, 2013265921u, 1811939329u,
                                             1711276033u, 1224736769u, 1107296257u};
 constexpr uint32_t kRoot[kPolyPowMaxPrimes] = {3u, 5u, 31u, 13u, 29u, 3u, 10u};
+static_assert(kQ[0] < 2ull * kQ[kPolyPowMaxPrimes - 1], "a residue mod an earlier prime reduces mod a later one by one subtraction");
 
 uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((unsigned __int128)a * b % q); }
 uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t q) {
@@ -672,6 +682,21 @@ size_t polypow_scratch_words(int d, int n, int nprimes) {
   return (size_t)N + 2 * kTwWords * (size_t)nprimes + (size_t)nprimes * tet(d * n + 1) + tet(d + 1) + 64;
 }
 
+// Rows of the first forward column pass (kp0 stages; 0: no column pass) that can hold input, and the words cleared
+// before the input is scattered: the input's indices are < d B^2 + 1, and the pass takes columns of stride
+// N / 2^kp0.  The shared-memory stage loop (kp0 = 1) reads every row, so the whole buffer is cleared then.
+struct PassRows {
+  int rows;
+  uint32_t cleared;
+};
+PassRows first_pass_rows(int d, int B, int logN, int kp0) {
+  const uint64_t N = 1ull << logN, bound = (uint64_t)d * B * B + 1;
+  if (kp0 < 2) return PassRows{1 << kp0, (uint32_t)N};
+  const uint64_t stride = N >> kp0;
+  const uint64_t rows = (bound + stride - 1) / stride;
+  return PassRows{(int)rows, (uint32_t)(rows * stride)};
+}
+
 void polypow_plan(int d, int n, int nprimes, uint64_t *transform_len, uint64_t *bytes) {
   const int B = d * n + 1;
   uint64_t N = 1;
@@ -684,10 +709,15 @@ void polypow_plan(int d, int n, int nprimes, uint64_t *transform_len, uint64_t *
   const uint64_t nlo = N < 4096 ? N : 4096, nhi = N >> kTwLoBits ? N >> kTwLoBits : 1;
   // per prime and direction: the lo and hi tables (one word each) and the R / 2 roots with their companions
   const uint64_t tables = 2 * 4 * (nlo + nhi + R);
-  const uint64_t per_prime = tables + 4 * N                  // clear the transform buffer
-                             + 4 * 2 * n_in                   // read the input, write it into the buffer
-                             + (uint64_t)(2 * n_outer + 1) * 8 * N   // every pass reads and writes the buffer
-                             + 8 * n_out;                     // gather: read a residue, write it
+  // the first (outermost) pass takes min(8, logN - inner) stages, as polypow_launch splits them
+  const int outer0 = logN - inner < kPassMaxStages ? logN - inner : kPassMaxStages;
+  const PassRows PR = first_pass_rows(d, B, logN, outer0);
+  // every pass reads and writes the buffer, except that the first forward pass reads only its leading rows
+  const uint64_t passes = n_outer ? 4 * (uint64_t)PR.cleared + 4 * N + (uint64_t)(2 * n_outer) * 8 * N : 8 * N;
+  const uint64_t per_prime = tables + 4 * (uint64_t)PR.cleared   // clear the leading rows
+                             + 4 * 2 * n_in                       // read the input, write it into the buffer
+                             + passes
+                             + 8 * n_out;                         // gather: read a residue, write it
   if (transform_len) *transform_len = N;
   if (bytes) *bytes = (uint64_t)nprimes * per_prime + n_out * (4ull * nprimes + 4ull * kPolyPowLimbs);
 }
@@ -713,12 +743,13 @@ TwTab plan_tables(uint32_t *tab, uint32_t w, uint32_t N, const PrimeQ &P, TableJ
 }
 
 // One column pass of kp stages: the register-phase kernel for kp >= 2, the shared-memory stage loop for kp = 1.
+// nz_rows: rows of every column the forward pass reads (the rest are zero); the stage loop reads them all.
 void column_pass(bool inv, int kp, uint32_t blocks, uint32_t *a, int logN, int logM, const TwTab &T, const PrimeQ &P,
-                 cudaStream_t st) {
+                 cudaStream_t st, int nz_rows) {
 #define QFS_COLUMN_PASS(KP)                                                                               \
   case KP:                                                                                                \
-    if (inv) ntt_column_regs<KP, true><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P);           \
-    else ntt_column_regs<KP, false><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P);              \
+    if (inv) ntt_column_regs<KP, true><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P, 1 << KP);  \
+    else ntt_column_regs<KP, false><<<blocks, kNttThreads, 0, st>>>(a, logN, logM, T, T, P, nz_rows);     \
     break;
   switch (kp) {
     QFS_COLUMN_PASS(2)
@@ -779,14 +810,18 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
     TI[j] = plan_tables(tw + 2 * kTwWords * (size_t)j + kTwWords, wi, N, PQ[j], J, njobs);
   }
   power_tables_kernel<<<dim3(16, njobs), block, 0, st>>>(J);
+  // the packed input occupies indices < d B^2 + 1, so the first forward pass (columns of stride N >> outer[0]) finds
+  // it in its leading rows only: those rows are cleared and read, the others are zero without a read
+  const PassRows PR = first_pass_rows(d, B, logN, n_outer ? outer[0] : 0);
   for (int j = 0; j < nprimes; ++j) {
     const PrimeQ &P = PQ[j];
-    zero_kernel<<<grid, block, 0, st>>>(a, N);
+    zero_kernel<<<grid, block, 0, st>>>(a, PR.cleared);
     scatter_kernel<<<64, block, 0, st>>>(coeffs_dev, d, B, a, P);
     // forward: outer passes on blocks of M = N, N / 2^kp0, ...; the inner pass fuses the powers and the inverse
     int logM = logN;
     for (int i = 0; i < n_outer; ++i) {
-      column_pass(false, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TF[j], P, st);
+      column_pass(false, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TF[j], P, st,
+                  i == 0 ? PR.rows : 1 << outer[i]);
       logM -= outer[i];
     }
     if (inner == kPassMaxStages && N >= (uint32_t)(kPassR * kPassCols)) {
@@ -798,7 +833,7 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
     }
     for (int i = n_outer - 1; i >= 0; --i) {
       logM += outer[i];
-      column_pass(true, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TI[j], P, st);
+      column_pass(true, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TI[j], P, st, 1 << outer[i]);
     }
     gather_kernel<<<grid, block, 0, st>>>(a, D, B, ninv[j], res + (size_t)j * n_out, P);
     cudaError_t e = cudaGetLastError();

@@ -87,7 +87,13 @@ def test_poly_power_plan_without_gpu():
         n_in, n_out = 969, (16 * n + 3) * (16 * n + 2) * (16 * n + 1) // 6
         R = min(256, N)
         tables = 2 * 4 * (min(N, 4096) + max(1, N >> 12) + R)
-        per_prime = tables + 4 * N + 8 * n_in + (2 * k + 1) * 8 * N + 8 * n_out
+        # the input sits below index 16 B^2 + 1, so the first forward pass (columns of stride N >> kp0, kp0 =
+        # min(8, logN - inner)) clears and reads only the rows that can hold it
+        kp0 = min(8, logN - inner)
+        stride = N >> kp0
+        cleared = -(-(16 * B * B + 1) // stride) * stride
+        passes = 4 * cleared + 4 * N + 2 * k * 8 * N
+        per_prime = tables + 4 * cleared + 8 * n_in + passes + 8 * n_out
         assert info["hbm_bytes"] == need * per_prime + n_out * (4 * need + 32)
     with pytest.raises(RuntimeError):
         qfs.poly_power_info(16, f, 16)          # degree 256
