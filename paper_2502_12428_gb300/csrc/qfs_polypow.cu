@@ -565,15 +565,34 @@ __global__ void __launch_bounds__(kNttThreads) ntt_inner_regs(uint32_t *a, int l
   }
 }
 
-// residue of every output coefficient (packed descending lex, degree D = d n), times N^-1
+// The output monomials x2^e2 x3^e3 x4^e4 (e2 + e3 + e4 <= D) in transform order: e4, then e3, then e2, which is
+// contiguous in the packed transform (index e2 + B e3 + B^2 e4).  Row (e4, e3) holds D - e4 - e3 + 1 monomials and
+// starts at toff(D, e4, e3); rows are numbered e4-major, PB(e4) = e4 (D + 1) - tri(e4 - 1) of them before slice e4.
+__host__ __device__ __forceinline__ int toff(int D, int e4, int e3) {
+  const int n = D - e4;
+  return tet(D + 1) - tet(n + 1) + e3 * (n + 1) - tri(e3 - 1);
+}
+__device__ __forceinline__ int rows_before(int D, int e4) { return e4 * (D + 1) - tri(e4 - 1); }
+// row index -> (e4, e3): PB(e) = e (2D + 3 - e) / 2 <= r gives e from an integer square root, then corrections
+__device__ __forceinline__ void decode_row(int r, int D, int &e4, int &e3) {
+  const int b = 2 * D + 3;
+  int e = (b - isqrt(b * b - 8 * r)) >> 1;
+  while (e > 0 && rows_before(D, e) > r) --e;
+  while (rows_before(D, e + 1) <= r) ++e;
+  e4 = e;
+  e3 = r - rows_before(D, e);
+}
+
+// residue of every output coefficient, times N^-1, in transform order: one warp per row (e4, e3), lanes over e2,
+// so the reads of the transform and the writes of the residues are contiguous
 __global__ void gather_kernel(const uint32_t *a, int D, int B, uint32_t ninv, uint32_t *res, PrimeQ P) {
-  const int n_out = tet(D + 1);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_out; i += gridDim.x * blockDim.x) {
-    int u, s, t;
-    decode_packed(i, u, s, t);
-    const size_t idx = (size_t)(u - s) + (size_t)B * (s - t) + (size_t)B * B * t;
-    res[i] = mulmod(a[idx], ninv, P.q, P.mu);
-  }
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= tri(D + 1)) return;
+  int e4, e3;
+  decode_row(r, D, e4, e3);
+  const int o = toff(D, e4, e3), len = D - e4 - e3 + 1;
+  const uint32_t *row = a + (size_t)B * e3 + (size_t)B * B * e4;
+  for (int e2 = lane; e2 < len; e2 += 32) res[o + e2] = mulmod(row[e2], ninv, P.q, P.mu);
 }
 
 struct CrtParams {
@@ -586,11 +605,20 @@ struct CrtParams {
 // Garner: v_j = (...((r_j - v_0) q_0^-1 - v_1) q_1^-1 ... - v_{j-1}) q_{j-1}^-1 mod q_j; then
 // X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) in 8 little-endian 32-bit limbs.  v_k mod q_j for k < j is one conditional
 // subtraction: the primes are taken largest first and the largest is below twice the smallest, so v_k < 2 q_j.
-__global__ void crt_kernel(const uint32_t *res, int n_out, CrtParams C, uint32_t *out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_out; i += gridDim.x * blockDim.x) {
+// The residues are read in transform order (one warp per row, as the gather wrote them) and each coefficient is
+// written at its packed (descending lex) index tet(u) + tri(s) + t, (u, s, t) = (e2 + e3 + e4, e3 + e4, e4): one
+// 32-byte record per lane.
+__global__ void crt_kernel(const uint32_t *res, int n_out, int D, CrtParams C, uint32_t *out) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= tri(D + 1)) return;
+  int e4, e3;
+  decode_row(r, D, e4, e3);
+  const int o = toff(D, e4, e3), len = D - e4 - e3 + 1;
+  for (int e2 = lane; e2 < len; e2 += 32) {
+    const size_t i = (size_t)tet(e2 + e3 + e4) + tri(e3 + e4) + e4;
     uint32_t v[kPolyPowMaxPrimes];
     for (int j = 0; j < C.nprimes; ++j) {
-      uint32_t t = res[(size_t)j * n_out + i];
+      uint32_t t = res[(size_t)j * n_out + o + e2];
       for (int k = 0; k < j; ++k) {
         const uint32_t vk = v[k] >= C.q[j] ? v[k] - C.q[j] : v[k];
         t = mulmod(submod(t, vk, C.q[j]), C.inv[j][k], C.q[j], C.mu[j]);
@@ -608,7 +636,13 @@ __global__ void crt_kernel(const uint32_t *res, int n_out, CrtParams C, uint32_t
         carry = y >> 32;
       }
     }
-    for (int l = 0; l < kPolyPowLimbs; ++l) out[(size_t)i * kPolyPowLimbs + l] = x[l];
+    uint32_t *rec = out + i * kPolyPowLimbs;
+    if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {   // the record as two 16-byte stores
+      reinterpret_cast<uint4 *>(rec)[0] = make_uint4(x[0], x[1], x[2], x[3]);
+      reinterpret_cast<uint4 *>(rec)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+    } else {
+      for (int l = 0; l < kPolyPowLimbs; ++l) rec[l] = x[l];
+    }
   }
 }
 
@@ -617,6 +651,7 @@ constexpr uint32_t kQ[kPolyPowMaxPrimes] = {2130706433u, 2113929217u, 2013265921
                                             1711276033u, 1224736769u, 1107296257u};
 constexpr uint32_t kRoot[kPolyPowMaxPrimes] = {3u, 5u, 31u, 13u, 29u, 3u, 10u};
 static_assert(kQ[0] < 2ull * kQ[kPolyPowMaxPrimes - 1], "a residue mod an earlier prime reduces mod a later one by one subtraction");
+static_assert(kPolyPowLimbs == 8, "a coefficient record is two 16-byte stores");
 
 uint64_t host_mulmod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((unsigned __int128)a * b % q); }
 uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t q) {
@@ -835,11 +870,11 @@ cudaError_t polypow_launch(int d, int n, int nprimes, const uint32_t *coeffs_dev
       logM += outer[i];
       column_pass(true, outer[i], (N >> outer[i]) / kPassCols, a, logN, logM, TI[j], P, st, 1 << outer[i]);
     }
-    gather_kernel<<<grid, block, 0, st>>>(a, D, B, ninv[j], res + (size_t)j * n_out, P);
+    gather_kernel<<<(tri(D + 1) + 7) / 8, block, 0, st>>>(a, D, B, ninv[j], res + (size_t)j * n_out, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  crt_kernel<<<grid, block, 0, st>>>(res, n_out, C, out);
+  crt_kernel<<<(tri(D + 1) + 7) / 8, block, 0, st>>>(res, n_out, D, C, out);
   return cudaGetLastError();
 }
 
