@@ -535,7 +535,11 @@ def test_poly_power_multinomial_closed_form(qfs, d, n):
     assert got == [_multinomial(e) for e in oracle.form_monomials(d * n)]
 
 
-@pytest.mark.parametrize("d,n", [(4, 3), (16, 2), (16, 1)])
+# (d, n) chosen so that the transform length puts every pass size on the device: (1, 7) a one-stage column pass
+# (the shared-memory stage loop), (1, 9) two, (2, 5) three, (4, 3) four, (16, 1) five, (4, 5) six, (5, 6) seven,
+# (16, 2) eight; transforms of 2^13 words or more ((16, 1), (16, 2), (4, 5), (5, 6)) run the register-phase inner
+# pass, the shorter ones the shared-memory one
+@pytest.mark.parametrize("d,n", [(4, 3), (16, 2), (16, 1), (1, 7), (1, 9), (2, 5), (4, 5), (5, 6)])
 def test_poly_power_matches_definition(qfs, d, n):
     rng = np.random.default_rng(d * 100 + n)
     f = [int(x) for x in rng.integers(0, 5, len(oracle.form_monomials(d)))]
