@@ -744,6 +744,24 @@ def run_ncu_case(args):
                       "past_height_1": int((h.cpu().numpy() != 1).sum())}))
 
 
+def run_powering_case(args):
+    """A small fixed launch sequence for profilers: two calls of the exact powering f^n (the bench's degree-16 form
+    with coefficients in {0..4}), n = --ncu-powering."""
+    import torch
+    import paper_2502_12428_gb300.qfs as qfs
+    from paper_2502_12428_gb300 import build as qbuild
+    qbuild.build()
+    rng = np.random.default_rng(16)
+    f16 = rng.integers(0, 5, 969).astype(np.uint32)
+    npow = args.ncu_powering
+    n_out = (16 * npow + 3) * (16 * npow + 2) * (16 * npow + 1) // 6
+    limbs = torch.empty(n_out, 8, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        qfs.poly_power_limbs(16, f16, npow, out=limbs)
+    torch.cuda.synchronize()
+    print(json.dumps({"powering_case": f"deg16-n{npow}", "calls": 2, "output_terms": n_out}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -759,6 +777,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the sparse, mixed-prime and staged-engine lines")
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case and exit")
     ap.add_argument("--ncu-quartics", type=int, default=8192)
+    ap.add_argument("--ncu-powering", type=int, default=0,
+                    help="run two exact powerings f^n of the degree-16 bench form (the profiling case) and exit")
     ap.add_argument("--ncu-ctas", type=int, default=0)
     ap.add_argument("--engine", choices=["fused", "staged"], default=None, help="engine of the --ncu-case launch")
     ap.add_argument("--power", choices=["chain", "identity", "reduced"], default=None,
@@ -769,7 +789,7 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.gpus < 1:
         ap.error("--gpus must be at least 1")
-    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.ncu_case:
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.ncu_case and not args.ncu_powering:
         # not launched by torchrun: start the N ranks here, one per GPU
         if args.impl == "ours":
             import torch
@@ -779,7 +799,9 @@ def main():
         sys.exit(subprocess.call(torchrun_argv(args.gpus, sys.argv[1:], free_port())))
     if "WORLD_SIZE" in os.environ and int(os.environ["WORLD_SIZE"]) != args.gpus:
         ap.error(f"--gpus {args.gpus} does not match the launcher's WORLD_SIZE {os.environ['WORLD_SIZE']}")
-    if args.ncu_case:
+    if args.ncu_powering:
+        run_powering_case(args)
+    elif args.ncu_case:
         run_ncu_case(args)
     elif args.impl == "reference":
         run_reference(args)
