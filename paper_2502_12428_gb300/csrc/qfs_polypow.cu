@@ -35,11 +35,16 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, uint32_t q, u
   if (r >= q) r -= q;
   return (uint32_t)r;
 }
+// Corrections as an unsigned minimum: for x < 2q, min(x, x - q) is x mod q (x - q wraps above x when x < q).
 __device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t q) {
   const uint32_t s = a + b;   // a, b < q < 2^31: no overflow
-  return s >= q ? s - q : s;
+  return min(s, s - q);
 }
-__device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, uint32_t q) { return a >= b ? a - b : a + q - b; }
+// a - b mod q: d = a - b wraps to d + 2^32 when a < b, and then d + q (mod 2^32) = a - b + q is the smaller one
+__device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, uint32_t q) {
+  const uint32_t d = a - b;
+  return min(d, d + q);
+}
 __device__ __forceinline__ uint32_t powmod(uint32_t a, uint32_t e, uint32_t q, uint64_t mu) {
   uint32_t r = 1;
   while (e) {
@@ -64,7 +69,7 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const Prime
   const uint64_t t = (uint64_t)a * b;
   const uint32_t m = (uint32_t)t * P.qneg;
   const uint32_t u = (uint32_t)((t + (uint64_t)m * P.q) >> 32);
-  return u >= P.q ? u - P.q : u;
+  return min(u, u - P.q);
 }
 
 // a = 0, then the packed input reduced mod q
@@ -87,7 +92,7 @@ __global__ void scatter_kernel(const uint32_t *coeffs, int d, int B, uint32_t *a
 __device__ __forceinline__ uint32_t shoup_mul(uint32_t a, uint32_t w, uint32_t ws, uint32_t q) {
   const uint32_t est = __umulhi(a, ws);
   const uint32_t r = a * w - est * q;
-  return r >= q ? r - q : r;
+  return min(r, r - q);
 }
 
 // One power table of a batch: table[j] = base^(j step) for j < n, in Montgomery form (mont) or with Shoup
