@@ -12,12 +12,16 @@
 //      length-M transform into R-point transforms over columns of stride M / R, twiddles w_M^(c k) between
 //      passes); inside a pass the stages run in registers in two groups with one exchange through shared memory
 //      between them.  The last forward pass, the n-th powers and the first inverse pass share one kernel, so a
-//      length-2^24 transform pair costs five round trips through device memory instead of 48.
+//      length-2^24 transform pair costs five round trips through device memory instead of 48.  Only the leading
+//      rows of the first pass can hold input, so only they are cleared and read.
 //   3. Chinese remaindering (Garner's mixed-radix form) of the P residues of every coefficient into a 256-bit
 //      unsigned integer.  P is the smallest number of primes whose product exceeds the coefficient bound
-//      (sum of |coefficients|)^n, so the result is exact.
-// Modular products use Barrett reduction with mu = floor(2^64 / q), and Shoup's method (a precomputed
-// floor(w 2^32 / q) for each fixed multiplier w) for the twiddle factors.
+//      (sum of |coefficients|)^n, so the result is exact.  The residues are gathered and recombined by rows of the
+//      transform (contiguous reads), and each coefficient is written as one 32-byte record at its packed index.
+// Modular products: Shoup's method (a precomputed floor(w 2^32 / q) for each fixed multiplier w) for the roots
+// inside a pass, Montgomery products for the twiddles between passes and for the powers, Barrett reduction with
+// mu = floor(2^64 / q) in the gather and the remaindering.  Every correction of a value below 2q is an unsigned
+// minimum, min(x, x - q).
 #include <cuda_runtime.h>
 
 #include <cstdint>
